@@ -1,0 +1,176 @@
+/*
+ * mf_oracle.c -- CPU oracle for the sliding-window median filter.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the bench's
+ * CPU-baseline / reference arm may load this file's library.  The CUDA library
+ * shares no code with it: no header, no helper, no table.
+ *
+ * What it computes (paper Section 1, "Median filter"; Section 2, the trivial
+ * algorithm that finds the median of every window separately):
+ *
+ *   input  x[0 .. n-1], odd window size k = 2h + 1, 1 <= k <= n
+ *   output y[i] = median of (x[i], ..., x[i+k-1]) for i = 0 .. n-k
+ *
+ * The paper prints the output vector as (y_1, ..., x_{n-k+1}); the last entry
+ * is a typo for y_{n-k+1}: there are n-k+1 outputs, one per full window.
+ *
+ * The median is the element of rank h (0-based) in the window under the total
+ * order
+ *
+ *     a < b  <=>  key(x_a) < key(x_b)  or  (key(x_a) == key(x_b) and a < b)
+ *
+ * i.e. values compared first and ties broken by the element's index.  This is
+ * the order the paper's method works in: its piecewise sort is stable
+ * (Section 4.2, sorting the pairs (alpha[i], i) lexicographically) and, on
+ * ties between the two blocks, elements of the older block count as smaller
+ * (Section 5.3).  Because equal keys mean equal bits, y is unique; the index
+ * tie-break fixes only argmed, the index of the median element.
+ *
+ * Values: int32 are compared as signed integers.  float32 are compared by the
+ * IEEE 754-2008 totalOrder predicate (Section 5.10 of that standard): -NaN <
+ * -inf < negative numbers < -0 < +0 < positive numbers < +inf < +NaN, NaNs
+ * ordered by payload.  The paper only uses integers (Section 6.2); IEEE "<"
+ * would make -0 and +0 equal and let the result's bits depend on which of the
+ * two was picked, so the oracle never uses it.
+ *
+ * Method, per window: copy the k (value, index) pairs, sort them with the C
+ * library's qsort under the order above, output the element at rank h.  That
+ * is O(n k log k): slow and plain on purpose.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { MFO_INT32 = 0, MFO_FLOAT32 = 1 };
+
+typedef struct {
+    uint32_t bits;   /* the element's raw 32 bits */
+    int64_t index;   /* its position in x */
+} elem_t;
+
+/* IEEE 754 totalOrder on binary32 bit patterns: returns <0, 0, >0. */
+static int float_total_order(uint32_t a, uint32_t b)
+{
+    int neg_a = (int)(a >> 31), neg_b = (int)(b >> 31);
+    if (neg_a != neg_b)
+        return neg_a ? -1 : 1;              /* every negative precedes every positive */
+    if (a == b)
+        return 0;
+    if (!neg_a)                             /* both non-negative: larger magnitude is larger */
+        return a < b ? -1 : 1;
+    return a > b ? -1 : 1;                  /* both negative: larger magnitude is smaller */
+}
+
+static int int32_order(uint32_t a, uint32_t b)
+{
+    int32_t sa = (int32_t)a, sb = (int32_t)b;
+    return sa < sb ? -1 : (sa > sb ? 1 : 0);
+}
+
+static int cmp_int32(const void* pa, const void* pb)
+{
+    const elem_t* a = (const elem_t*)pa;
+    const elem_t* b = (const elem_t*)pb;
+    int c = int32_order(a->bits, b->bits);
+    if (c) return c;
+    return a->index < b->index ? -1 : (a->index > b->index ? 1 : 0);
+}
+
+static int cmp_float32(const void* pa, const void* pb)
+{
+    const elem_t* a = (const elem_t*)pa;
+    const elem_t* b = (const elem_t*)pb;
+    int c = float_total_order(a->bits, b->bits);
+    if (c) return c;
+    return a->index < b->index ? -1 : (a->index > b->index ? 1 : 0);
+}
+
+/* Median of the window that starts at x[start]; scratch holds k elements. */
+static void window_median(int dtype, const uint32_t* x, int64_t start, int32_t k,
+                          elem_t* scratch, uint32_t* y_out, int64_t* arg_out)
+{
+    for (int32_t t = 0; t < k; ++t) {
+        scratch[t].bits = x[start + t];
+        scratch[t].index = start + t;
+    }
+    qsort(scratch, (size_t)k, sizeof(elem_t), dtype == MFO_INT32 ? cmp_int32 : cmp_float32);
+    int32_t h = (k - 1) / 2;
+    *y_out = scratch[h].bits;
+    if (arg_out) *arg_out = scratch[h].index;
+}
+
+static int check_args(int dtype, const void* x, int64_t n, int32_t k)
+{
+    if (dtype != MFO_INT32 && dtype != MFO_FLOAT32) return -1;
+    if (!x || n < 1) return -2;
+    if (k < 1 || (k % 2) == 0 || (int64_t)k > n) return -3;
+    return 0;
+}
+
+/*
+ * Full filter: y[0 .. n-k] (raw 32-bit patterns), argmed optional (may be NULL).
+ * nthreads <= 0 lets OpenMP pick.  Returns 0, or a negative code on bad args.
+ */
+int mfo_filter(int dtype, const uint32_t* x, int64_t n, int32_t k,
+               uint32_t* y, int64_t* argmed, int nthreads)
+{
+    int rc = check_args(dtype, x, n, k);
+    if (rc) return rc;
+    int64_t m = n - k + 1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        elem_t* scratch = (elem_t*)malloc(sizeof(elem_t) * (size_t)k);
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int64_t i = 0; i < m; ++i)
+            window_median(dtype, x, i, k, scratch, &y[i], argmed ? &argmed[i] : NULL);
+        free(scratch);
+    }
+    return 0;
+}
+
+/*
+ * Sampled windows: for each requested start s = starts[j] (0 <= s <= n-k),
+ * y[j] = median of x[s .. s+k-1].  Used to check outputs of huge inputs one
+ * by one.  Returns -4 if a start is out of range.
+ */
+int mfo_windows(int dtype, const uint32_t* x, int64_t n, int32_t k,
+                const int64_t* starts, int64_t count,
+                uint32_t* y, int64_t* argmed, int nthreads)
+{
+    int rc = check_args(dtype, x, n, k);
+    if (rc) return rc;
+    for (int64_t j = 0; j < count; ++j)
+        if (starts[j] < 0 || starts[j] > n - k) return -4;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        elem_t* scratch = (elem_t*)malloc(sizeof(elem_t) * (size_t)k);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+        for (int64_t j = 0; j < count; ++j)
+            window_median(dtype, x, starts[j], k, scratch, &y[j], argmed ? &argmed[j] : NULL);
+        free(scratch);
+    }
+    return 0;
+}
+
+/* Number of threads an OpenMP parallel region would use (1 without OpenMP). */
+int mfo_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
