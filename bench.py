@@ -1,0 +1,367 @@
+"""Benchmark of the GB300 median filter: output Gsamples/s and % HBM roofline.
+
+Workload (one step = one median filter of one signal, the whole hot path:
+load, piecewise sort, pair post-processing, store):
+  float32 Gaussian random walk, n = 2^26, k = 1001 (seeded, synthetic).
+Also reported: the same n with int32 uniform [0, 2^31) (random input case).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank filters its own signal (seed + rank): the
+work is independent problems, weak scaling, no data-path collective; value
+is the samples of all ranks over the slowest rank's time.
+
+--impl reference times the CPU oracle (oracle/, per-window sort) on the host
+cores, on a bounded sample of windows of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import datetime as _dt
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIG = 1 << 26
+K_WIN = 1001
+METRIC = "output Gsamples/s at n=2^26, k=1001 (float32 random walk)"
+UNIT = "Gsamples/s"
+WORKLOAD = "float32 Gaussian random walk, n=2^26, k=1001"
+HBM_FALLBACK_GBS = 6800.0
+KERNEL_SOURCES = ["paper_1406_1717_gb300/csrc/mf_device.cuh",
+                  "paper_1406_1717_gb300/csrc/mf_fused.cu"]
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fused_kernel_randomwalk_n2p26_k1001.md")
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (host coordination only; no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, local, use_cuda):
+    if ws <= 1:
+        return None
+    import torch
+    import torch.distributed as dist
+    backend = "nccl" if use_cuda else "gloo"
+    if use_cuda:
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, dev=None):
+    if dist is not None:
+        if dev is not None:
+            dist.barrier(device_ids=[dev.index])
+        else:
+            dist.barrier()
+
+
+def reduce_max(dist, value, dev=None):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=dev if dev is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    m_t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_t or m_sha.group(1) != kernel_source_hash():
+        return None
+    return float(m_t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    ts = _dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, float(parts[1]), float(parts[2]), parts[4:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.file.name)
+        inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05] or rows
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3][1:5])
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside),
+                "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside)}
+
+
+def make_signal(kind, seed):
+    from signals import random_walk_f32, uniform_i32
+    return random_walk_f32(N_SIG, seed=seed) if kind == "walk" else uniform_i32(N_SIG, seed=seed)
+
+
+def cpu_oracle_rate(x, k, target_s, seed=0):
+    """Oracle windows/s on a bounded random sample of windows (all host cores)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    m = x.size - k + 1
+    pilot = rng.integers(0, m, size=4000)
+    t = time.perf_counter()
+    oracle.window_medians(x, k, pilot)
+    dt = max(time.perf_counter() - t, 1e-6)
+    count = int(max(4000, min(50_000_000, 4000 * target_s / dt)))
+    starts = rng.integers(0, m, size=count)
+    t = time.perf_counter()
+    oracle.window_medians(x, k, starts)
+    dt = time.perf_counter() - t
+    return count / dt, count, dt, oracle.max_threads()
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from signals import DEFAULT_SEED
+    x = make_signal("walk", DEFAULT_SEED)
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(1)
+    m = x.size - K_WIN + 1
+    per_step = args.ref_windows
+    for _ in range(args.warmup):
+        oracle.window_medians(x, K_WIN, rng.integers(0, m, size=per_step))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.window_medians(x, K_WIN, rng.integers(0, m, size=per_step))
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt / 1e9
+    cores = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_SIG, "k": K_WIN,
+                   "sample": f"{per_step} random windows per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} random windows of the workload per step, "
+                                   f"{args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    dist = init_dist(ws, local, True)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import paper_1406_1717_gb300 as mf
+    if not os.path.exists(mf.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    from signals import DEFAULT_SEED
+    seed = DEFAULT_SEED + rank
+
+    stream = torch.cuda.Stream(dev)
+    h = mf.mf_create(dev.index, stream)
+    k = K_WIN
+    m = N_SIG - k + 1
+
+    def device_run(kind):
+        x_np = make_signal(kind, seed)
+        x = torch.from_numpy(x_np).to(dev)
+        y = torch.empty(m, dtype=x.dtype, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                mf.mf_filter(h, x, k, y)
+        stream.synchronize()
+        barrier(dist, dev)
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        launches0 = mf.mf_launch_count(h)
+        t_wall0 = time.time()
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for s in range(args.steps):
+                mf.mf_filter(h, x, k, y)
+                ev[s + 1].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize(dev)
+        t_wall1 = time.time()
+        barrier(dist, dev)
+        launches = mf.mf_launch_count(h) - launches0
+        per = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+        total_ms = ev[0].elapsed_time(ev[-1])
+        del x, y
+        return x_np, total_ms, per, launches, (t_wall0, t_wall1)
+
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    x_walk, total_ms, per, launches, win = device_run("walk")
+    clocks = sampler.stop(*win)
+    total_ms_max = reduce_max(dist, total_ms, dev)
+    ms_per_step = total_ms_max / args.steps
+    value = ws * m * args.steps / (total_ms_max * 1e-3) / 1e9
+
+    # int32 uniform variant of the same size (random-input case)
+    _, total_i, per_i, _, _ = device_run("int")
+    total_i = reduce_max(dist, total_i, dev)
+    value_int = ws * m * args.steps / (total_i * 1e-3) / 1e9
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    xh = torch.from_numpy(x_walk).pin_memory()
+    yh = torch.empty(m, dtype=torch.float32).pin_memory()
+    xh_np, yh_np = xh.numpy(), yh.numpy()
+    e2e_steps = max(3, min(args.steps, 20))
+    mf.mf_filter_host(h, xh_np, k, yh_np)
+    barrier(dist, dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        mf.mf_filter_host(h, xh_np, k, yh_np)
+    e2e_s = reduce_max(dist, time.perf_counter() - t0, dev)
+    e2e_value = ws * m * e2e_steps / e2e_s / 1e9
+
+    peak, peak_kind = peaks()
+    alg_bytes = 4 * N_SIG + 4 * m
+    kernel_ms = total_ms / max(launches, 1)
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, count, dt, cores = cpu_oracle_rate(x_walk, k, args.cpu_seconds)
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{count} random windows of the workload ({dt:.1f} s of CPU work)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_SIG, "k": k, "signal_dtype": "float32",
+                   "seed": DEFAULT_SEED, "per_rank": "independent signal (seed + rank)",
+                   "l2": "inputs larger than L2 (268 MB input vs 129 MB L2), no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+        "int32_uniform": {"value": value_int, "unit": UNIT,
+                          "ms_per_step": total_i / args.steps,
+                          "p50_ms": float(np.percentile(per_i, 50))},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N_SIG,
+                "d2h_bytes_per_step": 4 * m, "steps": e2e_steps,
+                "entry": "mf_filter_host (pinned host buffers)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                     "kernel": "mf::fused_kernel",
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+    }
+    mf.mf_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-windows", type=int, default=100_000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

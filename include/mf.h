@@ -1,0 +1,148 @@
+/*
+ * mf.h -- C ABI of the GB300 (sm_103a) sliding-window median filter.
+ *
+ * The operation (paper "Median Filtering is Equivalent to Sorting", Section 1,
+ * "Median filter"): given x[0 .. n-1] and an odd window size k = 2h + 1,
+ * output y[i] = median(x[i], ..., x[i+k-1]) for i = 0 .. n-k ("valid" windows
+ * only, n-k+1 outputs; the paper defines no boundary padding).
+ *
+ * The median is the element of rank h under the order "value first, then
+ * index", so it is always one of the input elements and y carries its exact
+ * bits.  int32 values compare as signed integers; float32 values compare by
+ * IEEE 754 totalOrder on their bit patterns (-0 < +0, NaNs at the ends by
+ * sign), never by IEEE "<".  argmed[i] is the index of the median element in
+ * the signal (ties between equal values resolve to the lower index, which is
+ * what the paper's stable piecewise sort and its "older block first" rule in
+ * Section 5.3 give).
+ *
+ * Method (paper Sections 3-5): phase 1 sorts each block X_j = x[jk .. jk+k)
+ * stably (Section 3 "Piecewise Sorting", Section 4.2); phase 2 walks each
+ * adjacent block pair with two sorted doubly-linked lists, deleting the old
+ * block's elements and undoing the deletions of the new block's elements
+ * (Knuth's dancing links, Section 3 equations del / undo-del), and prints the
+ * smaller of the two lists' first large elements (Section 5.2).  Both phases
+ * run fused in CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions for every call below:
+ *  - "device pointer" means memory of the handle's device (cudaMalloc, torch
+ *    CUDA tensors, ...); "host pointer" means CPU memory.  The caller owns every
+ *    buffer it passes; the library owns only its handle and an internal
+ *    workspace inside the handle.
+ *  - Arrays are dense and contiguous, element type given by mf_dtype.
+ *  - Calls that take device pointers are asynchronous on the handle's stream
+ *    and return after enqueueing; errors raised while kernels run surface at
+ *    the next mf_sync (or any later call that synchronises).
+ *  - Arguments are checked before anything is enqueued; on a bad argument
+ *    nothing is launched and no output is written.
+ *  - A handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mf_ctx* mf_handle;
+
+typedef enum {
+    MF_OK = 0,
+    MF_ERR_NULL = 1,         /* a required pointer or the handle is NULL            */
+    MF_ERR_BAD_N = 2,        /* n < 1, or n too large for the requested outputs     */
+    MF_ERR_EVEN_K = 3,       /* k is even: the paper assumes k = 2h + 1 (Section 3) */
+    MF_ERR_K_GT_N = 4,       /* k < 1 or k > n: no full window                      */
+    MF_ERR_DTYPE = 5,        /* unknown mf_dtype                                    */
+    MF_ERR_OOM = 6,          /* workspace above max_workspace_bytes, or malloc fail */
+    MF_ERR_CUDA = 7,         /* a CUDA runtime call or kernel failed                */
+    MF_ERR_UNSUPPORTED = 8,  /* valid request this build does not implement         */
+    MF_ERR_OVERLAP = 9,      /* an output buffer overlaps an input buffer           */
+    MF_ERR_DEVICE = 10,      /* device index invalid or not an sm_103 GPU           */
+    MF_ERR_BAD_SEGMENT = 11  /* a batched segment descriptor is invalid             */
+} mf_status;
+
+typedef enum { MF_INT32 = 0, MF_FLOAT32 = 1 } mf_dtype;
+
+/* One signal of a batch.  Offsets are in elements from the x / y base
+ * pointers passed to mf_filter_batched; the signal is x[x_off .. x_off+n) and
+ * its n-k+1 outputs go to y[y_off ..].  pad must be 0. */
+typedef struct {
+    int64_t x_off;
+    int64_t n;
+    int64_t y_off;
+    int32_t k;
+    int32_t pad;
+} mf_segment;
+
+/* Create a handle bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  max_workspace_bytes
+ * caps the device workspace the handle may hold (0 = no cap).
+ * Errors: MF_ERR_NULL (out NULL), MF_ERR_DEVICE (no such device, or not
+ * compute capability 10.3), MF_ERR_CUDA.  On error *out is set to NULL. */
+mf_status mf_create(mf_handle* out, int device, void* cuda_stream, size_t max_workspace_bytes);
+
+/* Rebind the handle to another stream of the same device. */
+mf_status mf_set_stream(mf_handle h, void* cuda_stream);
+
+/* Median filter of one signal (paper Section 1; method Sections 3-5).
+ *  x       device pointer, n elements of `dtype` (input, not modified)
+ *  n       signal length, n >= k
+ *  k       odd window size, 1 <= k <= n (k <= 16383 in this build)
+ *  y       device pointer, n-k+1 elements of `dtype` (output, overwritten)
+ *  argmed  device pointer to n-k+1 int32 (output) or NULL; needs n <= 2^31-1
+ * y and argmed must not overlap x.
+ * Errors: MF_ERR_NULL, MF_ERR_DTYPE, MF_ERR_BAD_N, MF_ERR_EVEN_K,
+ * MF_ERR_K_GT_N, MF_ERR_OVERLAP, MF_ERR_UNSUPPORTED (k above the limit),
+ * MF_ERR_CUDA (launch failed). */
+mf_status mf_filter(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32_t k,
+                    void* y, int32_t* argmed);
+
+/* Same as mf_filter, but x, y and argmed are HOST pointers.  The call copies
+ * x to the handle's device workspace, filters, copies y (and argmed) back and
+ * waits for the stream: it is synchronous.  Pinned host memory gives the
+ * fastest copies; pageable memory works.
+ * Errors: as mf_filter, plus MF_ERR_OOM (workspace). */
+mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_t n, int32_t k,
+                         void* y_host, int32_t* argmed_host);
+
+/* Filter many independent signals in one call (all of one dtype).
+ *  x, y       device base pointers; signal s is x[segs[s].x_off ..+n) and
+ *             writes y[segs[s].y_off ..+ n-k+1)
+ *  segs_host  HOST array of nseg descriptors (copied before return)
+ *  argmed     device pointer parallel to y (index within each signal) or NULL
+ * Output ranges must not overlap each other or x.
+ * Errors: as mf_filter, plus MF_ERR_BAD_SEGMENT (naming no segment index:
+ * any invalid descriptor rejects the whole call), MF_ERR_OOM. */
+mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
+                            const mf_segment* segs_host, int32_t nseg, int32_t* argmed);
+
+/* Backward pass of y = median_filter(x): gx[j] = sum of gy[i] over the
+ * outputs i whose median element is j (argmed[i] == j), summed in ascending
+ * i, so the result is deterministic.  This is the gradient of y with respect
+ * to x wherever the window values are distinct.
+ *  gy      device pointer, n-k+1 float32 (upstream gradient)
+ *  argmed  device pointer, n-k+1 int32 from mf_filter of the same (n, k)
+ *  gx      device pointer, n float32 (output, overwritten)
+ * Errors: as mf_filter. */
+mf_status mf_filter_backward(mf_handle h, const float* gy, const int32_t* argmed,
+                             int64_t n, int32_t k, float* gx);
+
+/* Wait for the handle's stream; returns MF_ERR_CUDA if any enqueued work failed. */
+mf_status mf_sync(mf_handle h);
+
+/* Number of kernels this handle has launched since creation (for accounting). */
+mf_status mf_launch_count(mf_handle h, uint64_t* count);
+
+/* Static string naming a status code (never NULL). */
+const char* mf_status_str(mf_status s);
+
+/* Release the handle and its workspace (waits for its stream first). */
+mf_status mf_destroy(mf_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MF_H */

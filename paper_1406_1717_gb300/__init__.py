@@ -1,0 +1,229 @@
+"""GB300 (sm_103a) sliding-window median filter -- Python binding of libmf.so.
+
+The library implements "Median Filtering is Equivalent to Sorting"
+(Suomela): phase 1 sorts each length-k block, phase 2 post-processes every
+adjacent block pair with two sorted doubly-linked lists (dancing links).
+All arithmetic runs in the CUDA kernels of ``libmf.so``; this module only
+marshals arguments (tensor pointers, sizes, streams) into the C ABI declared
+in ``include/mf.h`` and turns status codes into exceptions.  There is no CPU
+fallback: if the library is missing, every call raises.
+
+Functions carry the C names: ``mf_create``, ``mf_set_stream``, ``mf_filter``,
+``mf_filter_host``, ``mf_filter_batched``, ``mf_filter_backward``,
+``mf_sync``, ``mf_launch_count``, ``mf_status_str``, ``mf_destroy``.
+``median_filter`` is a convenience wrapper that allocates the outputs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmf.so")
+
+MF_INT32, MF_FLOAT32 = 0, 1
+
+STATUS_NAMES = {
+    0: "MF_OK", 1: "MF_ERR_NULL", 2: "MF_ERR_BAD_N", 3: "MF_ERR_EVEN_K",
+    4: "MF_ERR_K_GT_N", 5: "MF_ERR_DTYPE", 6: "MF_ERR_OOM", 7: "MF_ERR_CUDA",
+    8: "MF_ERR_UNSUPPORTED", 9: "MF_ERR_OVERLAP", 10: "MF_ERR_DEVICE",
+    11: "MF_ERR_BAD_SEGMENT",
+}
+
+# mf_segment: int64 x_off, int64 n, int64 y_off, int32 k, int32 pad
+SEGMENT_DTYPE = np.dtype([("x_off", "<i8"), ("n", "<i8"), ("y_off", "<i8"),
+                          ("k", "<i4"), ("pad", "<i4")])
+
+
+class MFError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {mf_status_str(status)}" if what else mf_status_str(status))
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmf.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "or python -m paper_1406_1717_gb300.build")
+        lib = ctypes.CDLL(path)
+        c = ctypes
+        vp, i32, i64, sz = c.c_void_p, c.c_int32, c.c_int64, c.c_size_t
+        sig = {
+            "mf_create": ([c.POINTER(vp), c.c_int, vp, sz], c.c_int),
+            "mf_set_stream": ([vp, vp], c.c_int),
+            "mf_filter": ([vp, c.c_int, vp, i64, i32, vp, vp], c.c_int),
+            "mf_filter_host": ([vp, c.c_int, vp, i64, i32, vp, vp], c.c_int),
+            "mf_filter_batched": ([vp, c.c_int, vp, vp, vp, i32, vp], c.c_int),
+            "mf_filter_backward": ([vp, vp, vp, i64, i32, vp], c.c_int),
+            "mf_sync": ([vp], c.c_int),
+            "mf_launch_count": ([vp, c.POINTER(c.c_uint64)], c.c_int),
+            "mf_status_str": ([c.c_int], c.c_char_p),
+            "mf_destroy": ([vp], c.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise MFError(status, what)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.int32:
+        return MF_INT32
+    if t.dtype == torch.float32:
+        return MF_FLOAT32
+    raise TypeError(f"median filter supports int32 and float32, got {t.dtype}")
+
+
+def _dptr(t, name: str):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# ---------------------------------------------------------------------------
+# C-ABI functions
+# ---------------------------------------------------------------------------
+def mf_status_str(status: int) -> str:
+    try:
+        return load_library().mf_status_str(int(status)).decode()
+    except RuntimeError:
+        return STATUS_NAMES.get(int(status), f"status {status}")
+
+
+def mf_create(device: int = 0, stream=None, max_workspace_bytes: int = 0):
+    """Create a handle on CUDA device ``device`` bound to ``stream`` (torch
+    stream, raw cudaStream_t int, or None for the default stream)."""
+    h = ctypes.c_void_p()
+    _check(load_library().mf_create(ctypes.byref(h), int(device), _stream_ptr(stream),
+                                    int(max_workspace_bytes)), "mf_create")
+    return h
+
+
+def mf_set_stream(handle, stream):
+    _check(load_library().mf_set_stream(handle, _stream_ptr(stream)), "mf_set_stream")
+
+
+def mf_filter(handle, x, k: int, y, argmed=None):
+    """y[i] = median(x[i .. i+k-1]) on the device; x, y (and argmed, int32)
+    are contiguous CUDA tensors of the handle's device."""
+    _check(load_library().mf_filter(handle, _dtype_code(x), _dptr(x, "x"), x.numel(), int(k),
+                                    _dptr(y, "y"), _dptr(argmed, "argmed")), "mf_filter")
+
+
+def mf_filter_host(handle, x, k: int, y, argmed=None):
+    """Same as mf_filter with HOST arrays (numpy or CPU tensors); synchronous."""
+    def hptr(a):
+        if a is None:
+            return None
+        if isinstance(a, np.ndarray):
+            if not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host arrays must be contiguous")
+            return ctypes.c_void_p(a.ctypes.data)
+        return _dptr(a, "host tensor")
+    if isinstance(x, np.ndarray):
+        code = {np.dtype(np.int32): MF_INT32, np.dtype(np.float32): MF_FLOAT32}.get(x.dtype)
+        if code is None:
+            raise TypeError(f"median filter supports int32 and float32, got {x.dtype}")
+        n = x.size
+    else:
+        code, n = _dtype_code(x), x.numel()
+    _check(load_library().mf_filter_host(handle, code, hptr(x), n, int(k), hptr(y), hptr(argmed)),
+           "mf_filter_host")
+
+
+def make_segments(n, k, x_off, y_off) -> np.ndarray:
+    segs = np.zeros(len(n), dtype=SEGMENT_DTYPE)
+    segs["n"], segs["k"], segs["x_off"], segs["y_off"] = n, k, x_off, y_off
+    return segs
+
+
+def mf_filter_batched(handle, x, y, segs: np.ndarray, argmed=None):
+    """Filter many signals packed in x; ``segs`` is a numpy array of SEGMENT_DTYPE."""
+    segs = np.ascontiguousarray(segs, dtype=SEGMENT_DTYPE)
+    _check(load_library().mf_filter_batched(handle, _dtype_code(x), _dptr(x, "x"), _dptr(y, "y"),
+                                            ctypes.c_void_p(segs.ctypes.data), int(segs.size),
+                                            _dptr(argmed, "argmed")), "mf_filter_batched")
+
+
+def mf_filter_backward(handle, gy, argmed, n: int, k: int, gx):
+    """gx[j] = sum of gy[i] over argmed[i] == j (float32 tensors, int32 argmed)."""
+    _check(load_library().mf_filter_backward(handle, _dptr(gy, "gy"), _dptr(argmed, "argmed"),
+                                             int(n), int(k), _dptr(gx, "gx")),
+           "mf_filter_backward")
+
+
+def mf_sync(handle):
+    _check(load_library().mf_sync(handle), "mf_sync")
+
+
+def mf_launch_count(handle) -> int:
+    c = ctypes.c_uint64()
+    _check(load_library().mf_launch_count(handle, ctypes.byref(c)), "mf_launch_count")
+    return int(c.value)
+
+
+def mf_destroy(handle):
+    _check(load_library().mf_destroy(handle), "mf_destroy")
+
+
+# ---------------------------------------------------------------------------
+# convenience
+# ---------------------------------------------------------------------------
+_handles = {}
+
+
+def default_handle(device: int):
+    """One handle per device, bound to the default stream; call sites rebind
+    it to torch's current stream before use."""
+    h = _handles.get(device)
+    if h is None:
+        h = mf_create(device)
+        _handles[device] = h
+    return h
+
+
+def median_filter(x, k: int, return_argmed: bool = False):
+    """Median filter of a 1-D CUDA tensor on torch's current stream."""
+    import torch
+    if x.dim() != 1 or not x.is_cuda:
+        raise ValueError("x must be a 1-D CUDA tensor")
+    dev = x.device.index
+    h = default_handle(dev)
+    mf_set_stream(h, torch.cuda.current_stream(x.device))
+    m = x.numel() - int(k) + 1
+    if m < 1:
+        raise ValueError("need k <= len(x)")
+    y = torch.empty(m, dtype=x.dtype, device=x.device)
+    a = torch.empty(m, dtype=torch.int32, device=x.device) if return_argmed else None
+    mf_filter(h, x.contiguous(), k, y, a)
+    return (y, a) if return_argmed else y

@@ -1,0 +1,256 @@
+// mf_api.cu -- the C ABI declared in include/mf.h: handle, argument checks,
+// workspace, dispatch to the CUDA kernels.  No CPU fallback: every result is
+// computed by the kernels of this library.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cstdlib>
+#include <new>
+#include <vector>
+
+#include "mf.h"
+#include "mf_internal.h"
+
+struct mf_ctx {
+    int device;
+    cudaStream_t stream;
+    size_t max_ws;
+    void* ws;
+    size_t ws_size;
+    int num_sms;
+    int max_k;
+    uint64_t launches;
+};
+
+namespace {
+
+// Make `dev` current for the scope of a call and restore the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+    return na && nb && pa < pb + nb && pb < pa + na;
+}
+
+mf_status check_common(mf_handle h, int dtype, const void* x, int64_t n, int32_t k, const void* y) {
+    if (!h || !x || !y) return MF_ERR_NULL;
+    if (dtype != MF_INT32 && dtype != MF_FLOAT32) return MF_ERR_DTYPE;
+    if (n < 1) return MF_ERR_BAD_N;
+    if (k < 1) return MF_ERR_K_GT_N;
+    if (k % 2 == 0) return MF_ERR_EVEN_K;
+    if ((int64_t)k > n) return MF_ERR_K_GT_N;
+    return MF_OK;
+}
+
+mf_status ensure_workspace(mf_handle h, size_t bytes) {
+    if (h->ws_size >= bytes) return MF_OK;
+    if (h->max_ws && bytes > h->max_ws) return MF_ERR_OOM;
+    if (h->ws) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_size = 0;
+    }
+    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return MF_ERR_OOM;
+    }
+    h->ws_size = bytes;
+    return MF_OK;
+}
+
+mf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MF_OK : MF_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+mf_status mf_create(mf_handle* out, int device, void* cuda_stream, size_t max_workspace_bytes) {
+    if (!out) return MF_ERR_NULL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) { cudaGetLastError(); return MF_ERR_DEVICE; }
+    if (device < 0 || device >= count) return MF_ERR_DEVICE;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return MF_ERR_CUDA;
+    if (prop.major != 10 || prop.minor != 3) return MF_ERR_DEVICE;
+    DeviceGuard g(device);
+    if (!g.ok) return MF_ERR_CUDA;
+    if (mf::fused_setup() != cudaSuccess || mf::backward_setup() != cudaSuccess) return MF_ERR_CUDA;
+    mf_ctx* h = new (std::nothrow) mf_ctx();
+    if (!h) return MF_ERR_OOM;
+    h->device = device;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->max_ws = max_workspace_bytes;
+    h->ws = nullptr;
+    h->ws_size = 0;
+    h->num_sms = prop.multiProcessorCount;
+    h->max_k = mf::fused_max_k();
+    h->launches = 0;
+    *out = h;
+    return MF_OK;
+}
+
+mf_status mf_set_stream(mf_handle h, void* cuda_stream) {
+    if (!h) return MF_ERR_NULL;
+    h->stream = (cudaStream_t)cuda_stream;
+    return MF_OK;
+}
+
+mf_status mf_filter(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32_t k,
+                    void* y, int32_t* argmed) {
+    mf_status st = check_common(h, dtype, x, n, k, y);
+    if (st != MF_OK) return st;
+    if (argmed && n > (int64_t)INT32_MAX) return MF_ERR_BAD_N;
+    if (k > h->max_k) return MF_ERR_UNSUPPORTED;
+    const size_t m = (size_t)(n - k + 1);
+    if (overlaps(x, 4 * (size_t)n, y, 4 * m)) return MF_ERR_OVERLAP;
+    if (argmed && (overlaps(x, 4 * (size_t)n, argmed, 4 * m) || overlaps(y, 4 * m, argmed, 4 * m)))
+        return MF_ERR_OVERLAP;
+    DeviceGuard g(h->device);
+    if (!g.ok) return MF_ERR_CUDA;
+    return cuda_status(mf::launch_fused((const uint32_t*)x, n, k, dtype == MF_FLOAT32,
+                                        (uint32_t*)y, argmed, h->num_sms, h->stream,
+                                        &h->launches));
+}
+
+mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_t n, int32_t k,
+                         void* y_host, int32_t* argmed_host) {
+    mf_status st = check_common(h, dtype, x_host, n, k, y_host);
+    if (st != MF_OK) return st;
+    if (argmed_host && n > (int64_t)INT32_MAX) return MF_ERR_BAD_N;
+    if (k > h->max_k) return MF_ERR_UNSUPPORTED;
+    const size_t m = (size_t)(n - k + 1);
+    const size_t xb = (4 * (size_t)n + 255) & ~size_t(255);
+    const size_t yb = (4 * m + 255) & ~size_t(255);
+    DeviceGuard g(h->device);
+    if (!g.ok) return MF_ERR_CUDA;
+    st = ensure_workspace(h, xb + yb + (argmed_host ? yb : 0));
+    if (st != MF_OK) return st;
+    char* base = (char*)h->ws;
+    uint32_t* xd = (uint32_t*)base;
+    uint32_t* yd = (uint32_t*)(base + xb);
+    int32_t* ad = argmed_host ? (int32_t*)(base + xb + yb) : nullptr;
+    cudaError_t e = cudaMemcpyAsync(xd, x_host, 4 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = mf::launch_fused(xd, n, k, dtype == MF_FLOAT32, yd, ad, h->num_sms, h->stream,
+                             &h->launches);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(y_host, yd, 4 * m, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && ad)
+        e = cudaMemcpyAsync(argmed_host, ad, 4 * m, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_status(e);
+}
+
+mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
+                            const mf_segment* segs, int32_t nseg, int32_t* argmed) {
+    if (!h || !x || !y || (!segs && nseg > 0)) return MF_ERR_NULL;
+    if (dtype != MF_INT32 && dtype != MF_FLOAT32) return MF_ERR_DTYPE;
+    if (nseg < 0) return MF_ERR_BAD_SEGMENT;
+    int64_t xext = 0, yext = 0;
+    std::vector<std::pair<int64_t, int64_t>> yr;
+    yr.reserve((size_t)nseg);
+    for (int32_t s = 0; s < nseg; ++s) {
+        const mf_segment& d = segs[s];
+        if (d.pad != 0 || d.x_off < 0 || d.y_off < 0 || d.n < 1 || d.k < 1 || d.k % 2 == 0 ||
+            (int64_t)d.k > d.n || d.k > h->max_k)
+            return MF_ERR_BAD_SEGMENT;
+        if (argmed && d.n > (int64_t)INT32_MAX) return MF_ERR_BAD_SEGMENT;
+        const int64_t m = d.n - d.k + 1;
+        xext = std::max(xext, d.x_off + d.n);
+        yext = std::max(yext, d.y_off + m);
+        yr.emplace_back(d.y_off, d.y_off + m);
+    }
+    std::sort(yr.begin(), yr.end());
+    for (size_t i = 1; i < yr.size(); ++i)
+        if (yr[i].first < yr[i - 1].second) return MF_ERR_OVERLAP;
+    if (overlaps(x, 4 * (size_t)xext, y, 4 * (size_t)yext)) return MF_ERR_OVERLAP;
+    if (argmed && (overlaps(x, 4 * (size_t)xext, argmed, 4 * (size_t)yext) ||
+                   overlaps(y, 4 * (size_t)yext, argmed, 4 * (size_t)yext)))
+        return MF_ERR_OVERLAP;
+    DeviceGuard g(h->device);
+    if (!g.ok) return MF_ERR_CUDA;
+    const uint32_t* xb = (const uint32_t*)x;
+    uint32_t* yb = (uint32_t*)y;
+    for (int32_t s = 0; s < nseg; ++s) {
+        const mf_segment& d = segs[s];
+        cudaError_t e = mf::launch_fused(xb + d.x_off, d.n, d.k, dtype == MF_FLOAT32,
+                                         yb + d.y_off, argmed ? argmed + d.y_off : nullptr,
+                                         h->num_sms, h->stream, &h->launches);
+        if (e != cudaSuccess) return MF_ERR_CUDA;
+    }
+    return MF_OK;
+}
+
+mf_status mf_filter_backward(mf_handle h, const float* gy, const int32_t* argmed,
+                             int64_t n, int32_t k, float* gx) {
+    if (!h || !gy || !argmed || !gx) return MF_ERR_NULL;
+    if (n < 1 || n > (int64_t)INT32_MAX) return MF_ERR_BAD_N;
+    if (k < 1) return MF_ERR_K_GT_N;
+    if (k % 2 == 0) return MF_ERR_EVEN_K;
+    if ((int64_t)k > n) return MF_ERR_K_GT_N;
+    const size_t m = (size_t)(n - k + 1);
+    if (overlaps(gx, 4 * (size_t)n, gy, 4 * m) || overlaps(gx, 4 * (size_t)n, argmed, 4 * m))
+        return MF_ERR_OVERLAP;
+    DeviceGuard g(h->device);
+    if (!g.ok) return MF_ERR_CUDA;
+    cudaError_t e = mf::launch_backward(gy, argmed, n, k, gx, h->stream, &h->launches);
+    if (e == cudaErrorInvalidValue) return MF_ERR_UNSUPPORTED;
+    return cuda_status(e);
+}
+
+mf_status mf_sync(mf_handle h) {
+    if (!h) return MF_ERR_NULL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return MF_ERR_CUDA;
+    return cuda_status(cudaStreamSynchronize(h->stream));
+}
+
+mf_status mf_launch_count(mf_handle h, uint64_t* count) {
+    if (!h || !count) return MF_ERR_NULL;
+    *count = h->launches;
+    return MF_OK;
+}
+
+const char* mf_status_str(mf_status s) {
+    switch (s) {
+        case MF_OK: return "MF_OK";
+        case MF_ERR_NULL: return "MF_ERR_NULL: a required pointer or the handle is NULL";
+        case MF_ERR_BAD_N: return "MF_ERR_BAD_N: n < 1 or too large";
+        case MF_ERR_EVEN_K: return "MF_ERR_EVEN_K: window size must be odd";
+        case MF_ERR_K_GT_N: return "MF_ERR_K_GT_N: need 1 <= k <= n";
+        case MF_ERR_DTYPE: return "MF_ERR_DTYPE: unknown dtype";
+        case MF_ERR_OOM: return "MF_ERR_OOM: workspace allocation failed or above the cap";
+        case MF_ERR_CUDA: return "MF_ERR_CUDA: a CUDA call or kernel failed";
+        case MF_ERR_UNSUPPORTED: return "MF_ERR_UNSUPPORTED: not implemented in this build";
+        case MF_ERR_OVERLAP: return "MF_ERR_OVERLAP: output overlaps an input";
+        case MF_ERR_DEVICE: return "MF_ERR_DEVICE: no such device or not compute capability 10.3";
+        case MF_ERR_BAD_SEGMENT: return "MF_ERR_BAD_SEGMENT: invalid batched segment descriptor";
+    }
+    return "MF_ERR_UNKNOWN";
+}
+
+mf_status mf_destroy(mf_handle h) {
+    if (!h) return MF_ERR_NULL;
+    {
+        DeviceGuard g(h->device);
+        if (g.ok) {
+            cudaStreamSynchronize(h->stream);
+            if (h->ws) cudaFree(h->ws);
+        }
+    }
+    delete h;
+    return MF_OK;
+}
+
+}  // extern "C"

@@ -63,13 +63,24 @@ def uniform_i32(n: int, seed: int = DEFAULT_SEED) -> np.ndarray:
 
 
 def distinct_f32(n: int, seed: int = DEFAULT_SEED) -> np.ndarray:
-    """perm(0..n-1) * 1e-3 + N(0, 0.1), redrawn until every value is distinct."""
+    """perm(0..n-1) * 1e-3 + N(0, 0.1) in float32 with all values distinct.
+
+    At n = 65,536 float32 rounding makes a few hundred collisions certain, so
+    redrawing the whole signal never succeeds; instead the noise of the
+    samples that collide is redrawn until every value is distinct.
+    """
     rng = _rng(seed)
+    base = rng.permutation(n).astype(np.float64) * 1e-3
+    noise = rng.normal(0.0, 0.1, size=n)
     for _ in range(1000):
-        x = (rng.permutation(n).astype(np.float64) * 1e-3
-             + rng.normal(0.0, 0.1, size=n)).astype(np.float32)
-        if np.unique(x).size == n:
+        x = (base + noise).astype(np.float32)
+        order = np.argsort(x, kind="stable")
+        dup = np.zeros(n, dtype=bool)
+        same = x[order[1:]] == x[order[:-1]]
+        dup[order[1:][same]] = True
+        if not dup.any():
             return x
+        noise[dup] = rng.normal(0.0, 0.1, size=int(dup.sum()))
     raise RuntimeError("could not draw a distinct-valued signal")
 
 

@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar: bit-exact y (raw 32-bit patterns) and exact argmed for every case.
+Cases: the workload configurations (small uniform k=31; n=2^26 random walk
+and int32 uniform at k=1001, checked on sampled windows including every
+pair boundary of sampled pairs), block-boundary sizes n in {k, k+1, 2k-1,
+2k, 2k+1, bk, bk+r}, k at tier boundaries, special float values, int32
+extremes, heavy ties, the paper's generators, the lower-bound reduction
+(checked against numpy's sort, no oracle), host-buffer entry point,
+batched entry point and the backward pass.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1406_1717_gb300 as mf
+from signals import (PAPER_GENERATORS, batched_signals, distinct_f32, paper_generator,
+                     random_walk_f32, uniform_f32, uniform_i32)
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def handle():
+    mf.load_library()
+    h = mf.mf_create(0, torch.cuda.current_stream(DEV))
+    yield h
+    mf.mf_destroy(h)
+
+
+def gpu_filter(h, x_np, k, with_arg=True):
+    x = torch.from_numpy(np.ascontiguousarray(x_np)).to(DEV)
+    m = x_np.size - k + 1
+    y = torch.empty(m, dtype=x.dtype, device=DEV)
+    a = torch.full((m,), -7, dtype=torch.int32, device=DEV) if with_arg else None
+    mf.mf_filter(h, x, k, y, a)
+    mf.mf_sync(h)
+    return y.cpu().numpy(), (a.cpu().numpy().astype(np.int64) if with_arg else None)
+
+
+def assert_bits_equal(got, ref, what=""):
+    g, r = got.view(np.uint32), ref.view(np.uint32)
+    if not np.array_equal(g, r):
+        bad = np.nonzero(g != r)[0]
+        raise AssertionError(f"{what}: {bad.size} mismatches, first at {bad[:8]} "
+                             f"got {g[bad[:4]]} want {r[bad[:4]]}")
+
+
+def check_full(h, x, k, what=""):
+    y, a = gpu_filter(h, x, k)
+    ry, ra = oracle.median_filter(x, k)
+    assert_bits_equal(y, ry, what)
+    np.testing.assert_array_equal(a, ra, err_msg=what)
+
+
+# ---------------------------------------------------------------------------
+def test_small_uniform_k31_full(handle):
+    """n = 100,000 float32 U[0,1), k = 31: every output."""
+    check_full(handle, uniform_f32(100_000), 31, "uniform k=31")
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 31, 33, 63, 65, 127, 255, 1001, 1023, 1025, 2047, 4095])
+def test_block_boundary_sizes(handle, k):
+    rng = np.random.default_rng(k)
+    for n in sorted({k, k + 1, 2 * k - 1, 2 * k, 2 * k + 1, 5 * k, 5 * k + int(rng.integers(1, k + 1)),
+                     23 * k + 7}):
+        if n < k:
+            continue
+        check_full(handle, random_walk_f32(n, seed=n), k, f"walk n={n} k={k}")
+        check_full(handle, uniform_i32(n, seed=n + 1), k, f"int n={n} k={k}")
+
+
+@pytest.mark.parametrize("gen", PAPER_GENERATORS)
+@pytest.mark.parametrize("dtype", ["int32", "float32"])
+def test_paper_generators(handle, gen, dtype):
+    for k in (7, 101, 1001):
+        x = paper_generator(gen, 30_011, seed=k, dtype=dtype)
+        check_full(handle, x, k, f"{gen} {dtype} k={k}")
+
+
+def test_many_tiles_ragged_tail(handle):
+    for k in (31, 1001):
+        n = 61 * 1001 * 3 + 517
+        check_full(handle, random_walk_f32(n, seed=3), k, f"walk tiles k={k}")
+        check_full(handle, paper_generator("r-small", n, seed=4), k, f"r-small tiles k={k}")
+
+
+def test_float_special_values(handle):
+    rng = np.random.default_rng(0)
+    special = np.array([0x00000000, 0x80000000, 0x7f800000, 0xff800000, 0x7fc00000,
+                        0xffc00000, 0x7f800001, 0xff800001, 0x7fffffff, 0xffffffff,
+                        0x00000001, 0x80000001, 0x3f800000, 0xbf800000], dtype=np.uint32)
+    for k in (3, 31, 255):
+        bits = rng.choice(special, size=20_000)
+        x = bits.view(np.float32)
+        check_full(handle, x, k, f"specials k={k}")
+        mix = uniform_f32(20_000, seed=k).view(np.uint32).copy()
+        hit = rng.random(20_000) < 0.3
+        mix[hit] = rng.choice(special, size=int(hit.sum()))
+        check_full(handle, mix.view(np.float32), k, f"mixed specials k={k}")
+
+
+def test_int32_extremes_and_ties(handle):
+    rng = np.random.default_rng(1)
+    vals = np.array([-2 ** 31, 2 ** 31 - 1, 0, -1, 1], dtype=np.int32)
+    for k in (3, 63, 1001):
+        check_full(handle, rng.choice(vals, size=30_000), k, f"int extremes k={k}")
+    check_full(handle, np.full(10_000, 5, np.int32), 101, "constant")
+
+
+def test_impulse_noise_ties(handle):
+    b = batched_signals(nseg=8, seed=5)
+    for s in range(8):
+        x = b.x[b.x_off[s]:b.x_off[s] + b.n[s]]
+        check_full(handle, x, int(b.k[s]), f"impulse segment {s}")
+
+
+@pytest.mark.parametrize("h_", [1, 3, 15, 100, 500])
+def test_lower_bound_reduction_sorts(handle, h_):
+    """Paper Section 2: -inf x h, block of h+1, +inf x h -> outputs sort the block
+    (checked against numpy's sort only)."""
+    rng = np.random.default_rng(h_)
+    units = 400
+    k = 2 * h_ + 1
+    blocks = rng.random((units, h_ + 1), dtype=np.float32)
+    parts = []
+    for b in blocks:
+        parts += [np.full(h_, -np.inf, np.float32), b, np.full(h_, np.inf, np.float32)]
+    x = np.concatenate(parts)
+    y, _ = gpu_filter(handle, x, k, with_arg=False)
+    unit = 3 * h_ + 1
+    got = np.stack([y[u * unit:u * unit + h_ + 1] for u in range(units)])
+    np.testing.assert_array_equal(got, np.sort(blocks, axis=1))
+
+
+@pytest.mark.parametrize("kind", ["walk_f32", "uniform_i32"])
+def test_full_size_k1001_sampled(handle, kind):
+    """n = 2^26, k = 1001, the configuration the bench times: sampled outputs,
+    including both ends of every sampled block pair."""
+    n, k = 1 << 26, 1001
+    x = random_walk_f32(n) if kind == "walk_f32" else uniform_i32(n)
+    y, a = gpu_filter(handle, x, k)
+    rng = np.random.default_rng(123)
+    m = n - k + 1
+    pairs = rng.integers(1, (n + k - 1) // k, size=1500)
+    starts = np.concatenate([(pairs - 1) * k + 1, np.minimum((pairs - 1) * k + k, m - 1),
+                             rng.integers(0, m, size=3000), [0, m - 1]])
+    ry, ra = oracle.window_medians(x, k, starts)
+    assert_bits_equal(y[starts], ry, f"{kind} sampled")
+    np.testing.assert_array_equal(a[starts], ra)
+    # every output is an element of its window (cheap property over all outputs)
+    idx = np.arange(m)
+    assert ((a >= idx) & (a < idx + k)).all()
+    assert_bits_equal(y, x[a], "y == x[argmed]")
+
+
+def test_max_supported_k_and_unsupported(handle):
+    lib = mf.load_library()
+    kmax = None
+    for k in (16383, 8191, 6001, 5001, 4095):
+        x = uniform_f32(2 * k + 3, seed=k)
+        xd = torch.from_numpy(x).to(DEV)
+        yd = torch.empty(x.size - k + 1, device=DEV)
+        st = lib.mf_filter(handle, 1, xd.data_ptr(), x.size, k, yd.data_ptr(), None)
+        if st == 0:
+            kmax = k
+            mf.mf_sync(handle)
+            ry, _ = oracle.median_filter(x, k)
+            assert_bits_equal(yd.cpu().numpy(), ry, f"k={k}")
+            break
+        assert st == 8   # MF_ERR_UNSUPPORTED
+    assert kmax is not None and kmax >= 4095
+
+
+def test_argument_errors(handle):
+    lib = mf.load_library()
+    x = torch.zeros(100, device=DEV)
+    y = torch.zeros(100, device=DEV)
+    xp, yp = x.data_ptr(), y.data_ptr()
+    assert lib.mf_filter(handle, 1, xp, 100, 4, yp, None) == 3       # even k
+    assert lib.mf_filter(handle, 1, xp, 100, 101, yp, None) == 4     # k > n
+    assert lib.mf_filter(handle, 1, xp, 100, 0, yp, None) == 4       # k < 1
+    assert lib.mf_filter(handle, 1, xp, 0, 1, yp, None) == 2         # n < 1
+    assert lib.mf_filter(handle, 7, xp, 100, 3, yp, None) == 5       # dtype
+    assert lib.mf_filter(handle, 1, xp, 100, 3, xp + 8, None) == 9   # overlap
+    assert lib.mf_filter(handle, 1, None, 100, 3, yp, None) == 1     # null
+
+
+def test_host_entry_point_matches_device(handle):
+    x = random_walk_f32(300_007, seed=9)
+    k = 1001
+    y = np.empty(x.size - k + 1, np.float32)
+    a = np.empty(x.size - k + 1, np.int32)
+    mf.mf_filter_host(handle, x, k, y, a)
+    yd, ad = gpu_filter(handle, x, k)
+    assert_bits_equal(y, yd, "host vs device")
+    np.testing.assert_array_equal(a.astype(np.int64), ad)
+
+
+def test_batched_matches_oracle(handle):
+    b = batched_signals(nseg=64, seed=11, n_hi=20_000)
+    x = torch.from_numpy(b.x).to(DEV)
+    y = torch.empty(b.y_total, device=DEV)
+    a = torch.empty(b.y_total, dtype=torch.int32, device=DEV)
+    segs = mf.make_segments(b.n, b.k, b.x_off, b.y_off)
+    mf.mf_filter_batched(handle, x, y, segs, a)
+    mf.mf_sync(handle)
+    ry, ra = oracle.batched(b.x, b.n, b.k, b.x_off, b.y_off, b.y_total)
+    assert_bits_equal(y.cpu().numpy(), ry, "batched")
+    np.testing.assert_array_equal(a.cpu().numpy().astype(np.int64), ra)
+
+
+def test_backward_matches_oracle_gradient(handle):
+    n, k = 65_536, 63
+    x_np = distinct_f32(n, seed=2)
+    g_np = np.random.default_rng(3).standard_normal(n - k + 1).astype(np.float32)
+    _, a = gpu_filter(handle, x_np, k)
+    gy = torch.from_numpy(g_np).to(DEV)
+    ad = torch.from_numpy(a.astype(np.int32)).to(DEV)
+    gx = torch.empty(n, device=DEV)
+    mf.mf_filter_backward(handle, gy, ad, n, k, gx)
+    mf.mf_sync(handle)
+    _, ra = oracle.median_filter(x_np, k)
+    ref = oracle.median_gradient(g_np.astype(np.float64), ra, n)
+    # each gx[j] sums at most k float32 terms: bound the rounding by k * eps * sum|g|
+    absref = oracle.median_gradient(np.abs(g_np).astype(np.float64), ra, n)
+    np.testing.assert_array_less(np.abs(gx.cpu().numpy() - ref), k * 6e-8 * absref + 1e-30)
