@@ -40,7 +40,7 @@ UNIT = "Gsamples/s"
 WORKLOAD = "float32 Gaussian random walk, n=2^26, k=1001"
 HBM_FALLBACK_GBS = 6800.0
 KERNEL_SOURCES = ["paper_1406_1717_gb300/csrc/mf_device.cuh",
-                  "paper_1406_1717_gb300/csrc/mf_fused.cu"]
+                  "paper_1406_1717_gb300/csrc/mf_pipeline.cu"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fused_kernel_randomwalk_n2p26_k1001.md")
 
 

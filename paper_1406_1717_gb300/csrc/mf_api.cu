@@ -85,7 +85,7 @@ mf_status mf_create(mf_handle* out, int device, void* cuda_stream, size_t max_wo
     if (prop.major != 10 || prop.minor != 3) return MF_ERR_DEVICE;
     DeviceGuard g(device);
     if (!g.ok) return MF_ERR_CUDA;
-    if (mf::fused_setup() != cudaSuccess || mf::backward_setup() != cudaSuccess) return MF_ERR_CUDA;
+    if (mf::pipeline_setup() != cudaSuccess || mf::backward_setup() != cudaSuccess) return MF_ERR_CUDA;
     mf_ctx* h = new (std::nothrow) mf_ctx();
     if (!h) return MF_ERR_OOM;
     h->device = device;
@@ -94,7 +94,7 @@ mf_status mf_create(mf_handle* out, int device, void* cuda_stream, size_t max_wo
     h->ws = nullptr;
     h->ws_size = 0;
     h->num_sms = prop.multiProcessorCount;
-    h->max_k = mf::fused_max_k();
+    h->max_k = mf::pipeline_max_k();
     h->launches = 0;
     *out = h;
     return MF_OK;
@@ -118,9 +118,12 @@ mf_status mf_filter(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32
         return MF_ERR_OVERLAP;
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
-    return cuda_status(mf::launch_fused((const uint32_t*)x, n, k, dtype == MF_FLOAT32,
-                                        (uint32_t*)y, argmed, h->num_sms, h->stream,
-                                        &h->launches));
+    const size_t need = mf::pipeline_workspace_bytes(n, k);
+    st = ensure_workspace(h, need);
+    if (st != MF_OK) return st;
+    return cuda_status(mf::launch_pipeline((const uint32_t*)x, n, k, dtype == MF_FLOAT32,
+                                           (uint32_t*)y, argmed, h->ws, need, h->num_sms,
+                                           h->stream, &h->launches));
 }
 
 mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_t n, int32_t k,
@@ -134,7 +137,9 @@ mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_
     const size_t yb = (4 * m + 255) & ~size_t(255);
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
-    st = ensure_workspace(h, xb + yb + (argmed_host ? yb : 0));
+    const size_t io = xb + yb + (argmed_host ? yb : 0);
+    const size_t need = mf::pipeline_workspace_bytes(n, k);
+    st = ensure_workspace(h, io + need);
     if (st != MF_OK) return st;
     char* base = (char*)h->ws;
     uint32_t* xd = (uint32_t*)base;
@@ -142,8 +147,8 @@ mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_
     int32_t* ad = argmed_host ? (int32_t*)(base + xb + yb) : nullptr;
     cudaError_t e = cudaMemcpyAsync(xd, x_host, 4 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = mf::launch_fused(xd, n, k, dtype == MF_FLOAT32, yd, ad, h->num_sms, h->stream,
-                             &h->launches);
+        e = mf::launch_pipeline(xd, n, k, dtype == MF_FLOAT32, yd, ad, base + io, need,
+                                h->num_sms, h->stream, &h->launches);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(y_host, yd, 4 * m, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess && ad)
@@ -180,13 +185,18 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
         return MF_ERR_OVERLAP;
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
+    size_t need = 0;
+    for (int32_t s = 0; s < nseg; ++s)
+        need = std::max(need, mf::pipeline_workspace_bytes(segs[s].n, segs[s].k));
+    mf_status st = ensure_workspace(h, need);
+    if (st != MF_OK) return st;
     const uint32_t* xb = (const uint32_t*)x;
     uint32_t* yb = (uint32_t*)y;
     for (int32_t s = 0; s < nseg; ++s) {
         const mf_segment& d = segs[s];
-        cudaError_t e = mf::launch_fused(xb + d.x_off, d.n, d.k, dtype == MF_FLOAT32,
-                                         yb + d.y_off, argmed ? argmed + d.y_off : nullptr,
-                                         h->num_sms, h->stream, &h->launches);
+        cudaError_t e = mf::launch_pipeline(xb + d.x_off, d.n, d.k, dtype == MF_FLOAT32,
+                                            yb + d.y_off, argmed ? argmed + d.y_off : nullptr,
+                                            h->ws, need, h->num_sms, h->stream, &h->launches);
         if (e != cudaSuccess) return MF_ERR_CUDA;
     }
     return MF_OK;

@@ -6,28 +6,51 @@
 
 namespace mf {
 
-constexpr int kFusedThreads = 256;                 // 8 warps per CTA
 constexpr int kMaxSmemBytes = 227 * 1024;          // opt-in dynamic shared memory per CTA
 
-struct FusedParams {
-    const uint32_t* x;        // input bits (int32 or float32)
-    uint32_t* y;              // output bits
-    int32_t* argmed;          // optional output indices
-    int64_t n;
-    int64_t npairs;           // b - 1
-    int k, h, G, bpg;
+// ---- multi-kernel pipeline (mf_pipeline.cu) --------------------------------
+constexpr int kPipeThreads = 256;
+
+struct PipeParams {
+    const uint32_t* x;
+    uint32_t* y;
+    int32_t* argmed;
+    int64_t n, nblocks, npairs;
+    int k, h, kp;             // kp: k rounded up to a multiple of 8 (16-byte rows)
     bool is_float;
+    uint16_t* perm;           // [nblocks][kp] position of the t-th smallest
+    uint16_t* rnk;            // [nblocks][kp] rank of position p
+    uint32_t* slink;          // [nblocks][kp] sorted-order prev:16|next:16, sentinel k
+    uint32_t* ulink;          // [nblocks][kp] unwind-time prev:16|next:16, sentinel k+1
+    uint16_t* ja;             // [npairs][kp] joint rank of A's position p
+    uint16_t* jb;             // [npairs][kp] joint rank of B's position p
+    uint16_t* out;            // [npairs][kp] printed node at step i: isB << 15 | slot
+};
+struct SortPlan {
     uint32_t off_keyA, off_keyB, off_valA, off_valB, off_hist;
-    uint32_t off_rec, off_jpos, off_info;
-    uint32_t rec_stride, jpos_stride, info_stride;
+    int G, bpg;
+};
+struct UnwindPlan {
+    int lanes;                // blocks per warp (32, 16, ..., 1)
+    int nw, ns;               // bitset words, summary words
+    uint32_t words_per_warp;
+};
+struct ChainPlan {
+    bool packed;              // one 32-bit word per list node (k <= 1021)
+    int nwarps;
+    int pairs_per_cta;
+    int lanes[8];             // pairs handled by warp w (a power of two)
+    int pair_off[8];          // first pair of warp w within the CTA
+    uint32_t word_off[8];     // start of warp w's shared-memory slice (words)
+    uint32_t rec_words;       // k + 2
 };
 
-bool fused_plan(int k, int G, FusedParams* p, size_t* smem_bytes);
-int fused_max_k();
-cudaError_t fused_setup();
-cudaError_t launch_fused(const uint32_t* x, int64_t n, int k, bool is_float,
-                         uint32_t* y, int32_t* argmed, int num_sms, cudaStream_t stream,
-                         uint64_t* launches);
+int pipeline_max_k();
+size_t pipeline_workspace_bytes(int64_t n, int k);
+cudaError_t pipeline_setup();
+cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, bool is_float,
+                            uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes,
+                            int num_sms, cudaStream_t stream, uint64_t* launches);
 
 cudaError_t backward_setup();
 cudaError_t launch_backward(const float* gy, const int32_t* argmed, int64_t n, int k,

@@ -1,0 +1,642 @@
+// mf_pipeline.cu -- the median filter as a pipeline of four kernels.
+//
+// Paper: "Median Filtering is Equivalent to Sorting" (Suomela).
+//
+// The post-processing of a block pair (Section 5.2) is a chain of k dependent
+// steps whose lists must sit in shared memory; how many chains an SM can run
+// at once -- shared-memory bytes per chain -- sets the speed.  So everything
+// that is not the chain runs in separate, fully parallel kernels, and the
+// chain kernel keeps nothing in shared memory but the lists:
+//
+//   sortmerge_kernel  load x, stable sort of every block (Section 4.2), and
+//                     per block: perm (pi), rank (pi^-1) and the sorted-order
+//                     links in position space (construct, Section 4.3); per
+//                     pair: the rank of every element in the merged order of
+//                     the pair's two blocks ("joint rank", A first on ties).
+//   unwind_kernel     per block used as B: the links unwind(B) leaves behind
+//                     (Section 3 "Unwind"), i.e. for each position i the
+//                     nearest smaller and larger element among positions < i.
+//                     One lane per block; a two-level bitset of the ranks
+//                     seen so far answers both queries.
+//   chain_kernel      one lane per pair, 32 pairs per warp: delete(A, i),
+//                     undelete(B, i), advance, print min(peek) for every step
+//                     (Section 5.2), lists in shared memory.
+//   epilogue_kernel   node -> input element, coalesced stores of y / argmed.
+//
+// Node numbering ("slots"): node i of the pair's lists is position i of A
+// until step i deletes it, and position i of B from the moment step i
+// undeletes it (A only ever holds positions > i, B only positions <= i), plus
+// two sentinels k (A) and k+1 (B) -- the paper's arrays of length k+1
+// (Section 4.3), shared by A and B.  Comparisons use the joint rank of the
+// node's element (the pi^-1 form of Section 4.2, extended across the pair),
+// so "alpha[i] is small" is jr(i) < jr(m) and peek(A) <= peek(B) is
+// jr(mA) < jr(mB); the sentinels have rank 0xFFFF, above every element.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "mf_device.cuh"
+#include "mf_internal.h"
+
+namespace mf {
+
+
+// ===========================================================================
+// sortmerge_kernel
+// ===========================================================================
+__global__ void __launch_bounds__(kPipeThreads)
+sortmerge_kernel(PipeParams p, SortPlan sp)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* keyA = reinterpret_cast<uint32_t*>(smem + sp.off_keyA);
+    uint32_t* keyB = reinterpret_cast<uint32_t*>(smem + sp.off_keyB);
+    uint16_t* valA = reinterpret_cast<uint16_t*>(smem + sp.off_valA);
+    uint16_t* valB = reinterpret_cast<uint16_t*>(smem + sp.off_valB);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + sp.off_hist);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int W = blockDim.x >> 5;
+    const int k = p.k;
+    const int64_t j0 = 1 + (int64_t)blockIdx.x * sp.G;
+    const int64_t left = p.npairs - (j0 - 1);
+    const int npair = (int)(left < sp.G ? (left > 0 ? left : 0) : sp.G);
+    const int nblk = npair + 1;
+    const int64_t ebase = (j0 - 1) * (int64_t)k;
+    const int64_t rem = p.n - ebase;
+    const int E = (int)((int64_t)nblk * k < rem ? (int64_t)nblk * k : rem);
+
+    for (int e = tid; e < E; e += blockDim.x) {
+        keyA[e] = to_key(__ldg(p.x + ebase + e), p.is_float);
+        valA[e] = (uint16_t)e;
+    }
+    __syncthreads();
+
+    const int ngroups = (nblk + sp.bpg - 1) / sp.bpg;
+    for (int gi = warp; gi < ngroups; gi += W) {
+        const int b0 = gi * sp.bpg;
+        const int b1 = min(b0 + sp.bpg, nblk);
+        const int e0 = b0 * k;
+        const int e1 = min(b1 * k, E);
+        warp_sort_group(keyA + e0, valA + e0, keyB + e0, valB + e0,
+                        max(0, e1 - e0), e0, k, b1 - b0, hist + warp * 256);
+    }
+    __syncthreads();
+
+    // inverse permutation (rank of each position) into valB
+    for (int e = tid; e < E; e += blockDim.x) {
+        const int blk = e / k;
+        valB[valA[e]] = (uint16_t)(e - blk * k);
+    }
+    __syncthreads();
+
+    // per block owned by this CTA: perm, rank, sorted-order links (sentinel k)
+    const int lb0 = (j0 == 1) ? 0 : 1;
+    for (int e = lb0 * k + tid; e < E; e += blockDim.x) {
+        const int blk = e / k;
+        const int pos = e - blk * k;
+        const int bstart = blk * k;
+        const int NBb = min(k, E - bstart);
+        const int64_t gb = j0 - 1 + blk;
+        const size_t o = (size_t)gb * p.kp + pos;
+        p.perm[o] = (uint16_t)(valA[e] - bstart);                 // e = bstart + t
+        const int t = valB[e];
+        p.rnk[o] = (uint16_t)t;
+        const uint32_t pv = t > 0 ? (uint32_t)(valA[bstart + t - 1] - bstart) : (uint32_t)k;
+        const uint32_t nx = t + 1 < NBb ? (uint32_t)(valA[bstart + t + 1] - bstart) : (uint32_t)k;
+        p.slink[o] = (pv << 16) | nx;
+    }
+
+    // per pair: joint ranks by position (scratch in keyB, free after the sort)
+    uint16_t* jp = reinterpret_cast<uint16_t*>(keyB);
+    for (int g = warp; g < npair; g += W) {
+        const int NB = min(k, E - (g + 1) * k);
+        warp_merge_ranks(keyA + g * k, valA + g * k, k, g * k,
+                         keyA + (g + 1) * k, valA + (g + 1) * k, NB, (g + 1) * k,
+                         jp + (size_t)g * 2 * k, jp + (size_t)g * 2 * k + k);
+    }
+    __syncthreads();
+    for (int g = 0; g < npair; ++g) {
+        const int NB = min(k, E - (g + 1) * k);
+        const size_t q = (size_t)(j0 - 1 + g) * p.kp;
+        for (int i = tid; i < k; i += blockDim.x) p.ja[q + i] = jp[(size_t)g * 2 * k + i];
+        for (int i = tid; i < NB; i += blockDim.x) p.jb[q + i] = jp[(size_t)g * 2 * k + k + i];
+    }
+}
+
+// ===========================================================================
+// unwind_kernel: one lane per block j >= 1 (block j is B of pair j).
+// unwind(B) deletes positions NB-1 .. 0; when position i is deleted its list
+// holds exactly the positions 0..i, so its retained prev / next are the
+// nearest smaller / larger element among positions < i.  Walking positions
+// upward with a bitset of the ranks seen so far gives the same links:
+// prev = predecessor, next = successor of rank(i) in the set; missing ->
+// B's sentinel k+1.
+// ===========================================================================
+__global__ void __launch_bounds__(kPipeThreads)
+unwind_kernel(PipeParams p, UnwindPlan up)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = p.k;
+    const int64_t gb = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // per-lane bank-private bitsets: word index (x * 32 + lane) in the warp's slice
+    uint32_t* ws = reinterpret_cast<uint32_t*>(smem) + (size_t)warp * up.words_per_warp;
+    uint32_t* W0 = ws + lane;                                   // nw words: ranks seen
+    uint32_t* W1 = ws + (size_t)up.nw * 32 + lane;              // ns words: non-empty W0 words
+    if (gb >= p.nblocks) return;
+    const int NB = (int)min((int64_t)k, p.n - gb * (int64_t)k);
+    const uint16_t* perm = p.perm + (size_t)gb * p.kp;
+    const uint16_t* rnk = p.rnk + (size_t)gb * p.kp;
+    uint4* ul4 = reinterpret_cast<uint4*>(p.ulink + (size_t)gb * p.kp);
+    for (int w = 0; w < up.nw; ++w) W0[w * 32] = 0;
+    for (int s = 0; s < up.ns; ++s) W1[s * 32] = 0;
+    const uint32_t sentB = (uint32_t)k + 1;
+    const uint4* rk4 = reinterpret_cast<const uint4*>(rnk);
+    uint4 rv = __ldg(rk4);
+    uint4 rn = (NB > 8) ? __ldg(rk4 + 1) : rv;
+    uint32_t uo[4];
+    for (int i = 0; i < NB; ++i) {
+        if ((i & 7) == 0 && i > 0) {
+            rv = rn;
+            if (i + 8 < NB) rn = __ldg(rk4 + (i >> 3) + 1);
+        }
+        const uint32_t rw = (i & 6) == 0 ? rv.x : (i & 6) == 2 ? rv.y : (i & 6) == 4 ? rv.z : rv.w;
+        const int r = (int)((i & 1) ? rw >> 16 : rw & 0xffffu);
+        const int w = r >> 5, b = r & 31;
+        const uint32_t word = W0[w * 32];
+        int pred = -1, succ = -1;
+        uint32_t m = word & ((1u << b) - 1u);
+        if (m) {
+            pred = (w << 5) | (31 - __clz(m));
+        } else {
+            int s = w >> 5;
+            uint32_t sm = W1[s * 32] & ((1u << (w & 31)) - 1u);
+            while (true) {
+                if (sm) {
+                    const int ww = (s << 5) | (31 - __clz(sm));
+                    pred = (ww << 5) | (31 - __clz(W0[ww * 32]));
+                    break;
+                }
+                if (--s < 0) break;
+                sm = W1[s * 32];
+            }
+        }
+        m = b == 31 ? 0u : (word & ~((2u << b) - 1u));
+        if (m) {
+            succ = (w << 5) | (__ffs(m) - 1);
+        } else {
+            int s = w >> 5;
+            const int wb = w & 31;
+            uint32_t sm = wb == 31 ? 0u : (W1[s * 32] & ~((2u << wb) - 1u));
+            while (true) {
+                if (sm) {
+                    const int ww = (s << 5) | (__ffs(sm) - 1);
+                    succ = (ww << 5) | (__ffs(W0[ww * 32]) - 1);
+                    break;
+                }
+                if (++s >= up.ns) break;
+                sm = W1[s * 32];
+            }
+        }
+        W0[w * 32] = word | (1u << b);
+        W1[(w >> 5) * 32] |= 1u << (w & 31);
+        const uint32_t pv = pred >= 0 ? (uint32_t)__ldg(perm + pred) : sentB;
+        const uint32_t nx = succ >= 0 ? (uint32_t)__ldg(perm + succ) : sentB;
+        uo[i & 3] = (pv << 16) | nx;
+        if ((i & 3) == 3) ul4[i >> 2] = make_uint4(uo[0], uo[1], uo[2], uo[3]);
+    }
+    if (NB & 3) {                                   // flush the partial last group
+        for (int t = NB & 3; t < 4; ++t) uo[t] = 0;
+        ul4[(NB - 1) >> 2] = make_uint4(uo[0], uo[1], uo[2], uo[3]);
+    }
+}
+
+// ===========================================================================
+// chain_kernel: the post-processing of Section 5.2, one lane per block pair.
+// Shared memory per lane (bank-private, word index x * NL + lane):
+//   rec[0 .. k+1]   prev:16 | next:16 (node numbers = slots, see top)
+//   jr [0 .. k+1]   joint rank of the node's current element (u16, two per word)
+// Besides m, each list caches in registers prev(m) and next(m) and their
+// ranks, so the moves of a step need no shared-memory load; the loads that
+// refill the caches are not on the step-to-step dependency path.
+// ===========================================================================
+// Per-lane view of the lists in shared memory.  Slot e's word sits at word
+// index e * NL + lane of the warp's slice, so every lane owns one bank.
+//   PACKED (k <= 1021): next:10 | prev:10 | joint rank:11 in one word
+//   wide             : next:16 | prev:16, joint rank in a separate u16 array
+// Relinks never read the word: when delete(A, i) unlinks i, next(prev(i)) is
+// i and prev(next(i)) is i; when undelete(B, i) relinks i between p and n,
+// next(p) is n and prev(n) is p.  So each relink is one XOR of old ^ new into
+// the field (equations del / undo-del of Section 3).
+template <bool PACKED>
+struct Lists {
+    static constexpr int PSH = PACKED ? 10 : 16;
+    static constexpr uint32_t FM = PACKED ? 0x3ffu : 0xffffu;
+    static constexpr uint32_t RINF = PACKED ? 0x7ffu : 0xffffu;
+    uint32_t* w;
+    uint16_t* jr16;
+    int NL;
+    __device__ __forceinline__ uint32_t ld(uint32_t e) const { return w[(size_t)e * NL]; }
+    __device__ __forceinline__ void st(uint32_t e, uint32_t v) const { w[(size_t)e * NL] = v; }
+    __device__ __forceinline__ void xr(uint32_t e, uint32_t v) const { atomicXor(&w[(size_t)e * NL], v); }
+    __device__ __forceinline__ uint16_t& JR(uint32_t e) const { return jr16[(size_t)(e >> 1) * 2 * NL + (e & 1)]; }
+    __device__ __forceinline__ static uint32_t nxt(uint32_t v) { return v & FM; }
+    __device__ __forceinline__ static uint32_t prv(uint32_t v) { return (v >> PSH) & FM; }
+    // rank of slot e whose word is v
+    __device__ __forceinline__ uint32_t rank(uint32_t e, uint32_t v) const {
+        if (PACKED) return v >> 20;
+        return JR(e);
+    }
+    __device__ __forceinline__ static uint32_t make(uint32_t prev, uint32_t next, uint32_t r) {
+        return PACKED ? (next | (prev << 10) | (r << 20)) : (next | (prev << 16));
+    }
+};
+
+// State of the two block data structures (Section 4.3): m, its list word,
+// its joint rank, and s.
+struct PairState {
+    uint32_t mA, wmA, rmA;
+    uint32_t mB, wmB, rmB;
+    int sA, sB;
+};
+
+// One step i of the post-processing (Section 5.2), branch-free: delete(A, i),
+// undelete(B, i), advance if s_A + s_B < h, return the printed node
+// (isB << 15 | slot).  wa is slot i's current word (loaded after the previous
+// step's last store); the next step's word is loaded into *wnext.
+template <bool PACKED>
+__device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>& L, uint32_t i,
+                                              uint32_t wa, uint32_t pb, uint32_t nb, uint32_t rb,
+                                              int h, uint32_t* wnext)
+{
+    using LL = Lists<PACKED>;
+    // -------- delete(A, i) ----------------------------------------------------
+    const uint32_t pa = LL::prv(wa), na = LL::nxt(wa);
+    const uint32_t ra = L.rank(i, wa);
+    L.xr(pa, i ^ na);                                   // next[prev[i]] <- next[i]
+    L.xr(na, (i ^ pa) << LL::PSH);                      // prev[next[i]] <- prev[i]
+    st.wmA ^= (pa == st.mA) ? (i ^ na) : 0u;            // keep m's cached word exact
+    st.wmA ^= (na == st.mA) ? ((i ^ pa) << LL::PSH) : 0u;
+    if (PACKED) st.rmA = st.wmA >> 20;
+    const bool small = ra < st.rmA;                     // alpha[i] small (or m at the end)
+    const bool isM = (i == st.mA);
+    const bool sApos = st.sA > 0;
+    // large & m == i: m <- next, then prev if s > 0  => pa (s > 0) or na
+    // large & m != i & s > 0: m <- prev[m]
+    const uint32_t tA = isM ? (sApos ? pa : na) : LL::prv(st.wmA);
+    const bool chgA = !small && (isM || sApos);
+    const uint32_t wtA = L.ld(tA);
+    uint32_t rtA = 0;
+    if (!PACKED) rtA = L.rank(tA, wtA);
+    st.mA = chgA ? tA : st.mA;
+    st.wmA = chgA ? wtA : st.wmA;
+    if (PACKED) st.rmA = st.wmA >> 20; else st.rmA = chgA ? rtA : st.rmA;
+    st.sA -= (small || sApos) ? 1 : 0;                  // s <- max(0, s - 1)
+    // -------- undelete(B, i) ----------------------------------------------------
+    L.st(i, LL::make(pb, nb, rb));
+    if (!PACKED) L.JR(i) = (uint16_t)rb;
+    L.xr(pb, nb ^ i);                                   // next[prev[i]] <- i
+    L.xr(nb, (pb ^ i) << LL::PSH);                      // prev[next[i]] <- i
+    st.wmB ^= (pb == st.mB) ? (nb ^ i) : 0u;
+    st.wmB ^= (nb == st.mB) ? ((pb ^ i) << LL::PSH) : 0u;
+    const bool smallB = rb < st.rmB;                    // small: m <- prev[m]
+    const uint32_t tB = LL::prv(st.wmB);
+    const uint32_t wtB = L.ld(tB);
+    uint32_t rtB = 0;
+    if (!PACKED) rtB = L.rank(tB, wtB);
+    *wnext = L.ld(i + 1);                               // all of step i's stores are issued
+    st.mB = smallB ? tB : st.mB;
+    st.wmB = smallB ? wtB : st.wmB;
+    if (PACKED) st.rmB = st.wmB >> 20; else st.rmB = smallB ? rtB : st.rmB;
+    // -------- advance the list whose first large element is smaller -----------
+    const bool adv = st.sA + st.sB < h;
+    const bool aA = st.rmA < st.rmB;                    // peek(A) <= peek(B): A first on ties
+    const uint32_t tN = aA ? LL::nxt(st.wmA) : LL::nxt(st.wmB);
+    const uint32_t wN = L.ld(tN);
+    uint32_t rN = 0;
+    if (!PACKED) rN = L.rank(tN, wN);
+    const bool advA = adv && aA, advB = adv && !aA;
+    st.mA = advA ? tN : st.mA;
+    st.wmA = advA ? wN : st.wmA;
+    st.mB = advB ? tN : st.mB;
+    st.wmB = advB ? wN : st.wmB;
+    if (PACKED) {
+        st.rmA = st.wmA >> 20;
+        st.rmB = st.wmB >> 20;
+    } else {
+        st.rmA = advA ? rN : st.rmA;
+        st.rmB = advB ? rN : st.rmB;
+    }
+    st.sA += advA ? 1 : 0;
+    st.sB += advB ? 1 : 0;
+    // -------- print min(peek(A), peek(B)) ------------------------------------
+    return st.rmA < st.rmB ? st.mA : (0x8000u | st.mB);
+}
+
+template <bool PACKED>
+__global__ void __launch_bounds__(kPipeThreads)
+chain_kernel(PipeParams p, ChainPlan cp)
+{
+    using LL = Lists<PACKED>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int NL = cp.lanes[warp];
+    if (lane >= NL) return;
+    const int64_t q = (int64_t)blockIdx.x * cp.pairs_per_cta + cp.pair_off[warp] + lane;
+    if (q >= p.npairs) return;                          // pair j = q + 1
+    const int k = p.k, h = p.h;
+    const int NB = (int)min((int64_t)k, p.n - (q + 1) * (int64_t)k);
+    uint32_t* wsl = reinterpret_cast<uint32_t*>(smem) + cp.word_off[warp];
+    LL L;
+    L.w = wsl + lane;
+    L.jr16 = reinterpret_cast<uint16_t*>(wsl + (size_t)cp.rec_words * NL + lane);
+    L.NL = NL;
+
+    // ---- construct(A) in slot space + empty B (rows of kp elements) ----------
+    const size_t abase = (size_t)q * p.kp;              // block j-1 = q
+    const size_t bbase = (size_t)(q + 1) * p.kp;
+    const uint4* sl4 = reinterpret_cast<const uint4*>(p.slink + abase);
+    const uint4* ja4 = reinterpret_cast<const uint4*>(p.ja + abase);
+    const int nchunk = p.kp >> 3;
+#pragma unroll 4
+    for (int c = 0; c < nchunk; ++c) {
+        const uint4 s0 = __ldg(sl4 + 2 * c), s1 = __ldg(sl4 + 2 * c + 1), jv = __ldg(ja4 + c);
+        const uint32_t sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+        const uint32_t jw[4] = {jv.x, jv.y, jv.z, jv.w};
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int e = 8 * c + t;
+            if (e < k) {
+                const uint32_t r = t & 1 ? jw[t >> 1] >> 16 : jw[t >> 1] & 0xffffu;
+                L.st(e, LL::make(sv[t] >> 16, sv[t] & 0xffffu, r));
+                if (!PACKED) L.JR(e) = (uint16_t)r;
+            }
+        }
+    }
+    const uint32_t SA = (uint32_t)k, SB = (uint32_t)k + 1;
+    const uint16_t* permA = p.perm + abase;
+    L.st(SA, LL::make(__ldg(permA + k - 1), __ldg(permA), LL::RINF));
+    L.st(SB, LL::make(SB, SB, LL::RINF));
+    if (!PACKED) { L.JR(SA) = (uint16_t)LL::RINF; L.JR(SB) = (uint16_t)LL::RINF; }
+
+    PairState st;
+    st.mA = __ldg(permA + h);
+    st.wmA = L.ld(st.mA);
+    st.rmA = L.rank(st.mA, st.wmA);
+    st.sA = h;
+    st.mB = SB;
+    st.wmB = L.ld(SB);
+    st.rmB = LL::RINF;
+    st.sB = 0;
+
+    // ---- the k steps, 8 at a time; inputs of the next two chunks in flight ---
+    const uint4* ul4 = reinterpret_cast<const uint4*>(p.ulink + bbase);
+    const uint4* jb4 = reinterpret_cast<const uint4*>(p.jb + (size_t)q * p.kp);
+    uint4* out4 = reinterpret_cast<uint4*>(p.out + (size_t)q * p.kp);
+    const int nch = (NB + 7) >> 3;
+    uint4 u0 = __ldg(ul4), u1 = __ldg(ul4 + 1), jv = __ldg(jb4);
+    uint4 v0 = u0, v1 = u1, kv = jv;
+    if (nch > 1) { v0 = __ldg(ul4 + 2); v1 = __ldg(ul4 + 3); kv = __ldg(jb4 + 1); }
+    uint32_t wa = L.ld(0);
+    for (int c = 0; c < nch; ++c) {
+        uint4 x0 = v0, x1 = v1, xv = kv;
+        if (c + 2 < nch) {
+            x0 = __ldg(ul4 + 2 * (c + 2));
+            x1 = __ldg(ul4 + 2 * (c + 2) + 1);
+            xv = __ldg(jb4 + (c + 2));
+        }
+        const uint32_t wbv[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+        const uint32_t jw[4] = {jv.x, jv.y, jv.z, jv.w};
+        uint32_t ov[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int i = 8 * c + t;
+            if (i < NB) {
+                const uint32_t rb = t & 1 ? jw[t >> 1] >> 16 : jw[t >> 1] & 0xffffu;
+                uint32_t wn;
+                const uint32_t o = pair_step<PACKED>(st, L, (uint32_t)i, wa, wbv[t] >> 16,
+                                                     wbv[t] & 0xffffu, rb, h, &wn);
+                wa = wn;
+                ov[t >> 1] |= (t & 1) ? (o << 16) : o;
+            }
+        }
+        out4[c] = make_uint4(ov[0], ov[1], ov[2], ov[3]);
+        u0 = v0; u1 = v1; jv = kv;
+        v0 = x0; v1 = x1; kv = xv;
+    }
+}
+
+// ===========================================================================
+// epilogue_kernel: y[(j-1)k + 1 + i] = the element printed at step i of pair
+// j, read from a shared-memory copy of the CTA's input span; y[0] = X_0[P_0[h]].
+// ===========================================================================
+__global__ void __launch_bounds__(kPipeThreads)
+epilogue_kernel(PipeParams p, int G)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* xs = reinterpret_cast<uint32_t*>(smem);
+    const int k = p.k;
+    const int64_t j0 = 1 + (int64_t)blockIdx.x * G;
+    const int64_t left = p.npairs - (j0 - 1);
+    const int npair = (int)(left < G ? (left > 0 ? left : 0) : G);
+    const int64_t ebase = (j0 - 1) * (int64_t)k;
+    const int64_t rem = p.n - ebase;
+    const int E = (int)((int64_t)(npair + 1) * k < rem ? (int64_t)(npair + 1) * k : rem);
+    for (int e = threadIdx.x; e < E; e += blockDim.x) xs[e] = __ldg(p.x + ebase + e);
+    __syncthreads();
+    const int nout = npair > 0 ? E - k : 0;
+    uint32_t* ys = p.y + ebase + 1;
+    int32_t* as = p.argmed ? p.argmed + ebase + 1 : nullptr;
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        const int g = o / k;
+        const int i = o - g * k;
+        const uint32_t id = p.out[(size_t)(j0 - 1 + g) * p.kp + i];
+        const int e = (g + (int)(id >> 15)) * k + (int)(id & 0x7fffu);
+        ys[o] = xs[e];
+        if (as) as[o] = (int32_t)(ebase + e);
+    }
+    if (j0 == 1 && threadIdx.x == 0) {
+        const int pm = p.perm[p.h];
+        p.y[0] = xs[pm];
+        if (p.argmed) p.argmed[0] = pm;
+    }
+}
+
+// ===========================================================================
+// host side
+// ===========================================================================
+static inline uint64_t al16(uint64_t v) { return (v + 15) & ~uint64_t(15); }
+static inline uint64_t al256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
+
+static bool sort_plan(int k, int G, SortPlan* sp, size_t* bytes)
+{
+    const int W = kPipeThreads / 32;
+    const uint64_t E = (uint64_t)(G + 1) * k;
+    if (E > 65535) return false;
+    uint64_t off = 0;
+    sp->off_keyA = (uint32_t)off; off = al16(off + 4 * E);
+    sp->off_keyB = (uint32_t)off; off = al16(off + 4 * E);
+    sp->off_valA = (uint32_t)off; off = al16(off + 2 * E);
+    sp->off_valB = (uint32_t)off; off = al16(off + 2 * E);
+    sp->off_hist = (uint32_t)off; off = al16(off + 1024ull * W);
+    *bytes = off;
+    return off <= (uint64_t)kMaxSmemBytes;
+}
+
+// Chain plan: per-lane words (k+2 list words, plus k/2+2 rank words when
+// not packed); warps are added greedily, each with the most lanes (32, 16,
+// ..., 1; a power of two keeps the layout bank-conflict free) that still fit.
+static bool chain_plan(int k, ChainPlan* cp, size_t* bytes)
+{
+    cp->packed = k <= 1021;
+    cp->rec_words = (uint32_t)(k + 2);
+    const uint32_t lane_words = cp->rec_words + (cp->packed ? 0u : (uint32_t)((k + 3) / 2));
+    const uint64_t budget = (uint64_t)kMaxSmemBytes / 4;       // words
+    uint64_t used = 0;
+    int nw = 0, pairs = 0;
+    while (nw < kPipeThreads / 32) {
+        int lanes = 32;
+        while (lanes > 0 && used + (uint64_t)lanes * lane_words > budget) lanes >>= 1;
+        if (lanes == 0) break;
+        cp->lanes[nw] = lanes;
+        cp->word_off[nw] = (uint32_t)used;
+        cp->pair_off[nw] = pairs;
+        used += (uint64_t)lanes * lane_words;
+        pairs += lanes;
+        ++nw;
+        if (lanes < 32 && lanes == 1) break;
+    }
+    cp->nwarps = nw;
+    cp->pairs_per_cta = pairs;
+    *bytes = (size_t)used * 4;
+    return nw > 0;
+}
+
+int pipeline_max_k()
+{
+    // limits: sort of one pair in shared memory, 15-bit slot numbers in the
+    // output ids, and a one-lane chain in shared memory
+    SortPlan sp;
+    size_t b;
+    int lo = 1, hi = 32765;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        ChainPlan cp;
+        size_t cb;
+        if (sort_plan(mid, 1, &sp, &b) && chain_plan(mid, &cp, &cb)) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+size_t pipeline_workspace_bytes(int64_t n, int k)
+{
+    const int64_t nblocks = (n + k - 1) / k;
+    const int64_t npairs = nblocks - 1;
+    const uint64_t kp = (uint64_t)((k + 7) & ~7);
+    uint64_t b = 0;
+    b += al256(2ull * nblocks * kp);     // perm
+    b += al256(2ull * nblocks * kp);     // rnk
+    b += al256(4ull * nblocks * kp);     // slink
+    b += al256(4ull * nblocks * kp);     // ulink
+    b += al256(2ull * (npairs > 0 ? npairs : 1) * kp) * 3;   // ja, jb, out
+    return (size_t)b;
+}
+
+cudaError_t pipeline_setup()
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(sortmerge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(unwind_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(chain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(chain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    return cudaFuncSetAttribute(epilogue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
+}
+
+cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, bool is_float,
+                            uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes,
+                            int num_sms, cudaStream_t stream, uint64_t* launches)
+{
+    if (ws_bytes < pipeline_workspace_bytes(n, k)) return cudaErrorInvalidValue;
+    PipeParams p{};
+    p.x = x; p.y = y; p.argmed = argmed;
+    p.n = n; p.k = k; p.h = (k - 1) / 2;
+    p.nblocks = (n + k - 1) / k;
+    p.npairs = p.nblocks - 1;
+    p.kp = (k + 7) & ~7;
+    p.is_float = is_float;
+    const uint64_t kp = (uint64_t)p.kp;
+    char* w = (char*)ws;
+    p.perm = (uint16_t*)w;  w += al256(2ull * p.nblocks * kp);
+    p.rnk = (uint16_t*)w;   w += al256(2ull * p.nblocks * kp);
+    p.slink = (uint32_t*)w; w += al256(4ull * p.nblocks * kp);
+    p.ulink = (uint32_t*)w; w += al256(4ull * p.nblocks * kp);
+    const uint64_t np1 = (uint64_t)(p.npairs > 0 ? p.npairs : 1);
+    p.ja = (uint16_t*)w;    w += al256(2ull * np1 * kp);
+    p.jb = (uint16_t*)w;    w += al256(2ull * np1 * kp);
+    p.out = (uint16_t*)w;
+
+    // ---- sortmerge: largest G that fits two CTAs per SM, else one ----------
+    SortPlan sp{};
+    size_t sbytes = 0;
+    int G = 0;
+    for (int g = 1; g <= 64; ++g) {
+        SortPlan t;
+        size_t b;
+        if (!sort_plan(k, g, &t, &b)) break;
+        if (b <= (size_t)kMaxSmemBytes / 2 || g == 1) G = g;
+    }
+    if (G == 0) return cudaErrorInvalidValue;
+    const int64_t want = (p.npairs + 2ll * num_sms - 1) / (2ll * num_sms);
+    if (want >= 1 && want < G) G = (int)want;
+    sort_plan(k, G, &sp, &sbytes);
+    sp.G = G;
+    const int W = kPipeThreads / 32;
+    int bpg = (G + 1 + W - 1) / W;
+    int cap = max(1, 2048 / k);
+    if (cap > 255) cap = 255;
+    sp.bpg = max(1, min(bpg, cap));
+    const int64_t sgrid = p.npairs > 0 ? (p.npairs + G - 1) / G : 1;
+    sortmerge_kernel<<<(unsigned)sgrid, kPipeThreads, sbytes, stream>>>(p, sp);
+    if (launches) *launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+
+    if (p.npairs > 0) {
+        // ---- unwind: one lane per block 1 .. b-1 ---------------------------
+        UnwindPlan up{};
+        up.nw = (k + 31) / 32;
+        up.ns = (up.nw + 31) / 32;
+        up.lanes = 32;
+        up.words_per_warp = (uint32_t)((up.nw + up.ns) * 32);
+        int uw = W;
+        while (uw > 1 && (size_t)up.words_per_warp * 4 * uw > (size_t)kMaxSmemBytes / 4) --uw;
+        const size_t ubytes = (size_t)up.words_per_warp * 4 * uw;
+        if (ubytes > (size_t)kMaxSmemBytes) return cudaErrorInvalidValue;
+        const int64_t nb1 = p.nblocks - 1;
+        const int64_t per_ucta = (int64_t)uw * 32;
+        const int64_t ugrid = (nb1 + per_ucta - 1) / per_ucta;
+        unwind_kernel<<<(unsigned)ugrid, 32 * uw, ubytes, stream>>>(p, up);
+        if (launches) *launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+        // ---- chain ----------------------------------------------------------
+        ChainPlan cp{};
+        size_t cbytes = 0;
+        if (!chain_plan(k, &cp, &cbytes)) return cudaErrorInvalidValue;
+        const int64_t cgrid = (p.npairs + cp.pairs_per_cta - 1) / cp.pairs_per_cta;
+        if (cp.packed)
+            chain_kernel<true><<<(unsigned)cgrid, 32 * cp.nwarps, cbytes, stream>>>(p, cp);
+        else
+            chain_kernel<false><<<(unsigned)cgrid, 32 * cp.nwarps, cbytes, stream>>>(p, cp);
+        if (launches) *launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+
+    // ---- epilogue -----------------------------------------------------------
+    int GE = max(1, min(16, 8192 / k));
+    const size_t ebytes = 4ull * (size_t)(GE + 1) * k;
+    const int64_t egrid = p.npairs > 0 ? (p.npairs + GE - 1) / GE : 1;
+    epilogue_kernel<<<(unsigned)egrid, kPipeThreads, ebytes, stream>>>(p, GE);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace mf
