@@ -60,7 +60,9 @@ typedef enum {
     MF_ERR_UNSUPPORTED = 8,  /* valid request this build does not implement         */
     MF_ERR_OVERLAP = 9,      /* an output buffer overlaps an input buffer           */
     MF_ERR_DEVICE = 10,      /* device index invalid or not an sm_103 GPU           */
-    MF_ERR_BAD_SEGMENT = 11  /* a batched segment descriptor is invalid             */
+    MF_ERR_BAD_SEGMENT = 11, /* a batched segment descriptor is invalid             */
+    MF_ERR_TOO_LARGE = 12    /* request needs more scratch than mf_filter_noalloc's
+                                fixed array holds                                   */
 } mf_status;
 
 typedef enum { MF_INT32 = 0, MF_FLOAT32 = 1 } mf_dtype;
@@ -128,6 +130,32 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
  * Errors: as mf_filter. */
 mf_status mf_filter_backward(mf_handle h, const float* gy, const int32_t* argmed,
                              int64_t n, int32_t k, float* gx);
+
+/* The median filter of mf_filter for callers that cannot call cudaMalloc.
+ * The paper has no counterpart: this entry point exists because some callers
+ * may not allocate device memory -- code that runs while a stream is being
+ * captured into a CUDA graph (cudaMalloc cannot be captured), programs whose
+ * device memory is handed out only by their own pool or arena, and real-time
+ * loops that cannot take an allocation's unbounded latency.  It needs no
+ * handle and allocates nothing: its scratch is a fixed 32 MiB device array
+ * inside the library, present on every GPU that loads libmf.so until the
+ * process exits.
+ *  x, n, k, y, argmed  as mf_filter (device pointers of the current device)
+ *  cuda_stream         cudaStream_t to run on (NULL = legacy default stream)
+ * Limits: the scratch a call needs is about 18 bytes per input sample
+ * (2 * 6 * kp bytes per block of k samples plus 6 * kp per block pair, kp = k
+ * rounded up to a multiple of 8), so n is limited to roughly 1.8 million;
+ * larger requests return MF_ERR_TOO_LARGE and launch nothing.
+ * The first call on a device, with that device current, looks up the
+ * array's device address and sets the kernels' limits; make that first call
+ * before any stream capture.  All calls share the one array: calls whose
+ * kernels overlap on the GPU (different streams, different host threads)
+ * race on it and must be serialised by the caller.  The array keeps the
+ * previous call's contents; the kernels write every scratch element before
+ * reading it, so nothing needs clearing.
+ * Errors: as mf_filter, plus MF_ERR_TOO_LARGE and MF_ERR_DEVICE. */
+mf_status mf_filter_noalloc(mf_dtype dtype, const void* x, int64_t n, int32_t k,
+                            void* y, int32_t* argmed, void* cuda_stream);
 
 /* Wait for the handle's stream; returns MF_ERR_CUDA if any enqueued work failed. */
 mf_status mf_sync(mf_handle h);

@@ -10,7 +10,7 @@ fallback: if the library is missing, every call raises.
 
 Functions carry the C names: ``mf_create``, ``mf_set_stream``, ``mf_filter``,
 ``mf_filter_host``, ``mf_filter_batched``, ``mf_filter_backward``,
-``mf_sync``, ``mf_launch_count``, ``mf_status_str``, ``mf_destroy``.
+``mf_filter_noalloc``, ``mf_sync``, ``mf_launch_count``, ``mf_status_str``, ``mf_destroy``.
 ``median_filter`` is a convenience wrapper that allocates the outputs.
 """
 from __future__ import annotations
@@ -30,7 +30,7 @@ STATUS_NAMES = {
     0: "MF_OK", 1: "MF_ERR_NULL", 2: "MF_ERR_BAD_N", 3: "MF_ERR_EVEN_K",
     4: "MF_ERR_K_GT_N", 5: "MF_ERR_DTYPE", 6: "MF_ERR_OOM", 7: "MF_ERR_CUDA",
     8: "MF_ERR_UNSUPPORTED", 9: "MF_ERR_OVERLAP", 10: "MF_ERR_DEVICE",
-    11: "MF_ERR_BAD_SEGMENT",
+    11: "MF_ERR_BAD_SEGMENT", 12: "MF_ERR_TOO_LARGE",
 }
 
 # mf_segment: int64 x_off, int64 n, int64 y_off, int32 k, int32 pad
@@ -67,6 +67,7 @@ def load_library(path: str = LIB_PATH):
             "mf_filter_host": ([vp, c.c_int, vp, i64, i32, vp, vp], c.c_int),
             "mf_filter_batched": ([vp, c.c_int, vp, vp, vp, i32, vp], c.c_int),
             "mf_filter_backward": ([vp, vp, vp, i64, i32, vp], c.c_int),
+            "mf_filter_noalloc": ([c.c_int, vp, i64, i32, vp, vp, vp], c.c_int),
             "mf_sync": ([vp], c.c_int),
             "mf_launch_count": ([vp, c.POINTER(c.c_uint64)], c.c_int),
             "mf_status_str": ([c.c_int], c.c_char_p),
@@ -180,6 +181,14 @@ def mf_filter_backward(handle, gy, argmed, n: int, k: int, gx):
     _check(load_library().mf_filter_backward(handle, _dptr(gy, "gy"), _dptr(argmed, "argmed"),
                                              int(n), int(k), _dptr(gx, "gx")),
            "mf_filter_backward")
+
+
+def mf_filter_noalloc(x, k: int, y, argmed=None, stream=None):
+    """mf_filter without a handle and without any device allocation (scratch
+    is a fixed array inside the library); for callers that cannot allocate."""
+    _check(load_library().mf_filter_noalloc(_dtype_code(x), _dptr(x, "x"), x.numel(), int(k),
+                                            _dptr(y, "y"), _dptr(argmed, "argmed"),
+                                            _stream_ptr(stream)), "mf_filter_noalloc")
 
 
 def mf_sync(handle):

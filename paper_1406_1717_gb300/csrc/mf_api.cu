@@ -246,6 +246,7 @@ const char* mf_status_str(mf_status s) {
         case MF_ERR_OVERLAP: return "MF_ERR_OVERLAP: output overlaps an input";
         case MF_ERR_DEVICE: return "MF_ERR_DEVICE: no such device or not compute capability 10.3";
         case MF_ERR_BAD_SEGMENT: return "MF_ERR_BAD_SEGMENT: invalid batched segment descriptor";
+        case MF_ERR_TOO_LARGE: return "MF_ERR_TOO_LARGE: request exceeds the fixed no-alloc scratch";
     }
     return "MF_ERR_UNKNOWN";
 }
