@@ -41,7 +41,7 @@ WORKLOAD = "float32 Gaussian random walk, n=2^26, k=1001"
 HBM_FALLBACK_GBS = 6800.0
 KERNEL_SOURCES = ["paper_1406_1717_gb300/csrc/mf_device.cuh",
                   "paper_1406_1717_gb300/csrc/mf_pipeline.cu"]
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fused_kernel_randomwalk_n2p26_k1001.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pipeline_randomwalk_n2p26_k1001.md")
 
 
 # ---------------------------------------------------------------------------
@@ -102,15 +102,15 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
     try:
         text = open(PROFILE_SUMMARY).read()
     except OSError:
         return None
     m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    m_t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_t = re.search(r"traffic_bytes_per_launch\[" + re.escape(kernel) + r"\]:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_t or m_sha.group(1) != kernel_source_hash():
         return None
     return float(m_t.group(1))
@@ -260,6 +260,7 @@ def run_ours(args):
         barrier(dist, dev)
         torch.cuda.synchronize(dev)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        mf.mf_set_timing(h, True)
         launches0 = mf.mf_launch_count(h)
         t_wall0 = time.time()
         with torch.cuda.stream(stream):
@@ -274,19 +275,22 @@ def run_ours(args):
         launches = mf.mf_launch_count(h) - launches0
         per = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
         total_ms = ev[0].elapsed_time(ev[-1])
+        ncalls = min(args.steps, 128)
+        kt = {name: v / ncalls for name, v in mf.mf_kernel_times(h, ncalls).items()}
+        mf.mf_set_timing(h, False)
         del x, y
-        return x_np, total_ms, per, launches, (t_wall0, t_wall1)
+        return x_np, total_ms, per, launches, (t_wall0, t_wall1), kt
 
     sampler = ClockSampler(dev.index)
     sampler.start()
-    x_walk, total_ms, per, launches, win = device_run("walk")
+    x_walk, total_ms, per, launches, win, kt = device_run("walk")
     clocks = sampler.stop(*win)
     total_ms_max = reduce_max(dist, total_ms, dev)
     ms_per_step = total_ms_max / args.steps
     value = ws * m * args.steps / (total_ms_max * 1e-3) / 1e9
 
     # int32 uniform variant of the same size (random-input case)
-    _, total_i, per_i, _, _ = device_run("int")
+    _, total_i, per_i, _, _, kt_i = device_run("int")
     total_i = reduce_max(dist, total_i, dev)
     value_int = ws * m * args.steps / (total_i * 1e-3) / 1e9
 
@@ -305,7 +309,8 @@ def run_ours(args):
 
     peak, peak_kind = peaks()
     alg_bytes = 4 * N_SIG + 4 * m
-    kernel_ms = total_ms / max(launches, 1)
+    dom = max(kt, key=kt.get)                     # dominant kernel, CUDA-event average
+    kernel_ms = kt[dom]
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
 
     cpu = None
@@ -325,15 +330,17 @@ def run_ours(args):
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "int32_uniform": {"value": value_int, "unit": UNIT,
                           "ms_per_step": total_i / args.steps,
-                          "p50_ms": float(np.percentile(per_i, 50))},
+                          "p50_ms": float(np.percentile(per_i, 50)), "kernels_ms": kt_i},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N_SIG,
                 "d2h_bytes_per_step": 4 * m, "steps": e2e_steps,
                 "entry": "mf_filter_host (pinned host buffers)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "frac": achieved / peak, "traffic": profiled_traffic(dom),
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": "mf::fused_kernel",
-                     "algorithmic_bytes_per_launch": alg_bytes},
+                     "kernel": dom, "kernel_ms": kernel_ms,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "step_frac": alg_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
+        "kernels_ms": kt,
         "clocks": clocks,
         "gpu_launches": launches,
         "cpu_baseline": cpu,

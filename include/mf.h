@@ -91,7 +91,8 @@ mf_status mf_set_stream(mf_handle h, void* cuda_stream);
 /* Median filter of one signal (paper Section 1; method Sections 3-5).
  *  x       device pointer, n elements of `dtype` (input, not modified)
  *  n       signal length, n >= k
- *  k       odd window size, 1 <= k <= n (k <= 16383 in this build)
+ *  k       odd window size, 1 <= k <= n (k <= 8004 in this build: one
+ *          block pair must fit in shared memory)
  *  y       device pointer, n-k+1 elements of `dtype` (output, overwritten)
  *  argmed  device pointer to n-k+1 int32 (output) or NULL; needs n <= 2^31-1
  * y and argmed must not overlap x.
@@ -142,9 +143,9 @@ mf_status mf_filter_backward(mf_handle h, const float* gy, const int32_t* argmed
  * process exits.
  *  x, n, k, y, argmed  as mf_filter (device pointers of the current device)
  *  cuda_stream         cudaStream_t to run on (NULL = legacy default stream)
- * Limits: the scratch a call needs is about 18 bytes per input sample
- * (2 * 6 * kp bytes per block of k samples plus 6 * kp per block pair, kp = k
- * rounded up to a multiple of 8), so n is limited to roughly 1.8 million;
+ * Limits: the scratch a call needs is about 14 bytes per input sample
+ * (8 * kp + 8 bytes per block of k samples plus 6 * kp per block pair, kp = k
+ * rounded up to a multiple of 8), so n is limited to roughly 2.3 million;
  * larger requests return MF_ERR_TOO_LARGE and launch nothing.
  * The first call on a device, with that device current, looks up the
  * array's device address and sets the kernels' limits; make that first call
@@ -162,6 +163,17 @@ mf_status mf_sync(mf_handle h);
 
 /* Number of kernels this handle has launched since creation (for accounting). */
 mf_status mf_launch_count(mf_handle h, uint64_t* count);
+
+/* Per-kernel timing for measurement.  With timing enabled, every mf_filter /
+ * mf_filter_host call records CUDA events on the handle's stream around its
+ * four kernels (sort+merge, unwind, post-processing chains, store), in a ring
+ * of the last 128 calls; enabling resets the ring. */
+mf_status mf_set_timing(mf_handle h, int enable);
+
+/* Sum of each kernel's duration (ms) over the last `ncalls` timed calls
+ * (at most 128): ms[0] sort+merge, ms[1] unwind, ms[2] chains, ms[3] store.
+ * Waits for those calls to finish. */
+mf_status mf_kernel_times(mf_handle h, int32_t ncalls, float* ms);
 
 /* Static string naming a status code (never NULL). */
 const char* mf_status_str(mf_status s);

@@ -10,7 +10,8 @@ fallback: if the library is missing, every call raises.
 
 Functions carry the C names: ``mf_create``, ``mf_set_stream``, ``mf_filter``,
 ``mf_filter_host``, ``mf_filter_batched``, ``mf_filter_backward``,
-``mf_filter_noalloc``, ``mf_sync``, ``mf_launch_count``, ``mf_status_str``, ``mf_destroy``.
+``mf_filter_noalloc``, ``mf_sync``, ``mf_launch_count``, ``mf_set_timing``,
+``mf_kernel_times``, ``mf_status_str``, ``mf_destroy``.
 ``median_filter`` is a convenience wrapper that allocates the outputs.
 """
 from __future__ import annotations
@@ -70,6 +71,8 @@ def load_library(path: str = LIB_PATH):
             "mf_filter_noalloc": ([c.c_int, vp, i64, i32, vp, vp, vp], c.c_int),
             "mf_sync": ([vp], c.c_int),
             "mf_launch_count": ([vp, c.POINTER(c.c_uint64)], c.c_int),
+            "mf_set_timing": ([vp, c.c_int], c.c_int),
+            "mf_kernel_times": ([vp, i32, c.POINTER(c.c_float)], c.c_int),
             "mf_status_str": ([c.c_int], c.c_char_p),
             "mf_destroy": ([vp], c.c_int),
         }
@@ -199,6 +202,20 @@ def mf_launch_count(handle) -> int:
     c = ctypes.c_uint64()
     _check(load_library().mf_launch_count(handle, ctypes.byref(c)), "mf_launch_count")
     return int(c.value)
+
+
+KERNEL_NAMES = ("sortmerge", "unwind", "chain", "epilogue")
+
+
+def mf_set_timing(handle, enable: bool = True):
+    _check(load_library().mf_set_timing(handle, 1 if enable else 0), "mf_set_timing")
+
+
+def mf_kernel_times(handle, ncalls: int) -> dict:
+    """Per-kernel milliseconds summed over the last ``ncalls`` timed calls."""
+    arr = (ctypes.c_float * 4)()
+    _check(load_library().mf_kernel_times(handle, int(ncalls), arr), "mf_kernel_times")
+    return dict(zip(KERNEL_NAMES, [float(v) for v in arr]))
 
 
 def mf_destroy(handle):

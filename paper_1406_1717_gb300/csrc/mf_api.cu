@@ -20,7 +20,8 @@ struct mf_ctx {
     size_t ws_size;
     int num_sms;
     int max_k;
-    uint64_t launches;
+    mf::LaunchStats stats;
+    bool events_made;
 };
 
 namespace {
@@ -95,7 +96,7 @@ mf_status mf_create(mf_handle* out, int device, void* cuda_stream, size_t max_wo
     h->ws_size = 0;
     h->num_sms = prop.multiProcessorCount;
     h->max_k = mf::pipeline_max_k();
-    h->launches = 0;
+    h->events_made = false;
     *out = h;
     return MF_OK;
 }
@@ -123,7 +124,7 @@ mf_status mf_filter(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32
     if (st != MF_OK) return st;
     return cuda_status(mf::launch_pipeline((const uint32_t*)x, n, k, dtype == MF_FLOAT32,
                                            (uint32_t*)y, argmed, h->ws, need, h->num_sms,
-                                           h->stream, &h->launches));
+                                           h->stream, &h->stats));
 }
 
 mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_t n, int32_t k,
@@ -148,7 +149,7 @@ mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_
     cudaError_t e = cudaMemcpyAsync(xd, x_host, 4 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = mf::launch_pipeline(xd, n, k, dtype == MF_FLOAT32, yd, ad, base + io, need,
-                                h->num_sms, h->stream, &h->launches);
+                                h->num_sms, h->stream, &h->stats);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(y_host, yd, 4 * m, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess && ad)
@@ -196,7 +197,7 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
         const mf_segment& d = segs[s];
         cudaError_t e = mf::launch_pipeline(xb + d.x_off, d.n, d.k, dtype == MF_FLOAT32,
                                             yb + d.y_off, argmed ? argmed + d.y_off : nullptr,
-                                            h->ws, need, h->num_sms, h->stream, &h->launches);
+                                            h->ws, need, h->num_sms, h->stream, &h->stats);
         if (e != cudaSuccess) return MF_ERR_CUDA;
     }
     return MF_OK;
@@ -214,7 +215,7 @@ mf_status mf_filter_backward(mf_handle h, const float* gy, const int32_t* argmed
         return MF_ERR_OVERLAP;
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
-    cudaError_t e = mf::launch_backward(gy, argmed, n, k, gx, h->stream, &h->launches);
+    cudaError_t e = mf::launch_backward(gy, argmed, n, k, gx, h->stream, &h->stats.launches);
     if (e == cudaErrorInvalidValue) return MF_ERR_UNSUPPORTED;
     return cuda_status(e);
 }
@@ -228,7 +229,44 @@ mf_status mf_sync(mf_handle h) {
 
 mf_status mf_launch_count(mf_handle h, uint64_t* count) {
     if (!h || !count) return MF_ERR_NULL;
-    *count = h->launches;
+    *count = h->stats.launches;
+    return MF_OK;
+}
+
+mf_status mf_set_timing(mf_handle h, int enable) {
+    if (!h) return MF_ERR_NULL;
+    if (enable && !h->events_made) {
+        DeviceGuard g(h->device);
+        if (!g.ok) return MF_ERR_CUDA;
+        for (int r = 0; r < mf::LaunchStats::kRing; ++r)
+            for (int j = 0; j < 5; ++j)
+                if (cudaEventCreate(&h->stats.ev[r][j]) != cudaSuccess) return MF_ERR_CUDA;
+        h->events_made = true;
+    }
+    h->stats.timing = enable != 0;
+    h->stats.ring_pos = 0;
+    return MF_OK;
+}
+
+mf_status mf_kernel_times(mf_handle h, int32_t ncalls, float* ms) {
+    if (!h || !ms) return MF_ERR_NULL;
+    for (int j = 0; j < 4; ++j) ms[j] = 0.0f;
+    if (!h->events_made || ncalls < 1) return MF_OK;
+    DeviceGuard g(h->device);
+    if (!g.ok) return MF_ERR_CUDA;
+    const uint64_t have = h->stats.ring_pos;
+    uint64_t use = (uint64_t)ncalls;
+    if (use > have) use = have;
+    if (use > (uint64_t)mf::LaunchStats::kRing) use = mf::LaunchStats::kRing;
+    for (uint64_t c = have - use; c < have; ++c) {
+        cudaEvent_t* ev = h->stats.ev[c % mf::LaunchStats::kRing];
+        if (cudaEventSynchronize(ev[4]) != cudaSuccess) return MF_ERR_CUDA;
+        for (int j = 0; j < 4; ++j) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, ev[j], ev[j + 1]) != cudaSuccess) return MF_ERR_CUDA;
+            ms[j] += t;
+        }
+    }
     return MF_OK;
 }
 
@@ -258,6 +296,9 @@ mf_status mf_destroy(mf_handle h) {
         if (g.ok) {
             cudaStreamSynchronize(h->stream);
             if (h->ws) cudaFree(h->ws);
+            if (h->events_made)
+                for (int r = 0; r < mf::LaunchStats::kRing; ++r)
+                    for (int j = 0; j < 5; ++j) cudaEventDestroy(h->stats.ev[r][j]);
         }
     }
     delete h;

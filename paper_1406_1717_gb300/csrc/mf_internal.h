@@ -31,18 +31,27 @@ struct SortPlan {
     int G, bpg;
 };
 struct UnwindPlan {
-    int lanes;                // blocks per warp (32, 16, ..., 1)
-    int nw, ns;               // bitset words, summary words
+    int segs, seglen;         // runs per block (1, 2, 4) and positions per run (multiple of 8)
+    int nw, ns;               // bitset words; summary words (0: one summary word in a register)
     uint32_t words_per_warp;
 };
 struct ChainPlan {
     bool packed;              // one 32-bit word per list node (k <= 1021)
     int nwarps;
     int pairs_per_cta;
-    int lanes[8];             // pairs handled by warp w (a power of two)
-    int pair_off[8];          // first pair of warp w within the CTA
-    uint32_t word_off[8];     // start of warp w's shared-memory slice (words)
+    uint32_t lanes_log2;      // 3 bits per warp: warp w handles 1 << field pairs
+    uint32_t lane_words;      // shared-memory words per pair
     uint32_t rec_words;       // k + 2
+};
+
+// Launch accounting of a handle: kernel count and, when timing is on, CUDA
+// events around the four kernels of each of the last kRing calls.
+struct LaunchStats {
+    static constexpr int kRing = 128;
+    uint64_t launches = 0;
+    bool timing = false;
+    uint64_t ring_pos = 0;
+    cudaEvent_t ev[kRing][5];
 };
 
 int pipeline_max_k();
@@ -50,7 +59,7 @@ size_t pipeline_workspace_bytes(int64_t n, int k);
 cudaError_t pipeline_setup();
 cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, bool is_float,
                             uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes,
-                            int num_sms, cudaStream_t stream, uint64_t* launches);
+                            int num_sms, cudaStream_t stream, LaunchStats* stats);
 
 cudaError_t backward_setup();
 cudaError_t launch_backward(const float* gy, const int32_t* argmed, int64_t n, int k,

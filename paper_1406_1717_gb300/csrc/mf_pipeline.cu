@@ -14,13 +14,10 @@
 //                     pair: the rank of every element in the merged order of
 //                     the pair's two blocks ("joint rank", A first on ties).
 //   unwind_kernel     per block used as B: the links unwind(B) leaves behind
-//                     (Section 3 "Unwind"), i.e. for each position i the
-//                     nearest smaller and larger element among positions < i.
-//                     One lane per block; a two-level bitset of the ranks
-//                     seen so far answers both queries.
-//   chain_kernel      one lane per pair, 32 pairs per warp: delete(A, i),
-//                     undelete(B, i), advance, print min(peek) for every step
-//                     (Section 5.2), lists in shared memory.
+//                     (Section 3, "Unwind"); one lane per block.
+//   chain_kernel      one lane per pair: delete(A, i), undelete(B, i),
+//                     advance, print min(peek) for every step (Section 5.2),
+//                     lists in shared memory.
 //   epilogue_kernel   node -> input element, coalesced stores of y / argmed.
 //
 // Node numbering ("slots"): node i of the pair's lists is position i of A
@@ -122,90 +119,142 @@ sortmerge_kernel(PipeParams p, SortPlan sp)
 }
 
 // ===========================================================================
-// unwind_kernel: one lane per block j >= 1 (block j is B of pair j).
-// unwind(B) deletes positions NB-1 .. 0; when position i is deleted its list
-// holds exactly the positions 0..i, so its retained prev / next are the
-// nearest smaller / larger element among positions < i.  Walking positions
-// upward with a bitset of the ranks seen so far gives the same links:
-// prev = predecessor, next = successor of rank(i) in the set; missing ->
-// B's sentinel k+1.
+// unwind_kernel: links of every block j >= 1 (block j is B of pair j).
+// unwind(B) (Section 3, "Unwind") deletes positions NB-1 .. 0; when position
+// i is deleted its list holds exactly positions 0..i, so the prev / next it
+// keeps are the nearest smaller / larger element among positions < i.
+// Walking positions upward with a bitset of the ranks seen so far gives the
+// same links: prev = predecessor, next = successor of rank(i) in the set,
+// mapped back to positions through the block's perm; missing -> B's
+// sentinel k+1.
+// A block's positions are split into S runs of seglen (a multiple of 8); run
+// s starts with the ranks of all positions before it already in its bitset,
+// so the S lanes of a block work independently and share one copy of the
+// block's perm in shared memory.  Lane l of a warp serves block slot l / S,
+// run l % S.  For k <= 1024 the summary of non-empty bitset words is one
+// register and the search has no branches.
 // ===========================================================================
+template <bool SMALL>
 __global__ void __launch_bounds__(kPipeThreads)
 unwind_kernel(PipeParams p, UnwindPlan up)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int S = up.segs, BPW = 32 / S;
+    const int bslot = lane / S, sg = lane - bslot * S;
     const int k = p.k;
-    const int64_t gb = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // per-lane bank-private bitsets: word index (x * 32 + lane) in the warp's slice
-    uint32_t* ws = reinterpret_cast<uint32_t*>(smem) + (size_t)warp * up.words_per_warp;
-    uint32_t* W0 = ws + lane;                                   // nw words: ranks seen
-    uint32_t* W1 = ws + (size_t)up.nw * 32 + lane;              // ns words: non-empty W0 words
-    if (gb >= p.nblocks) return;
-    const int NB = (int)min((int64_t)k, p.n - gb * (int64_t)k);
-    const uint16_t* perm = p.perm + (size_t)gb * p.kp;
-    const uint16_t* rnk = p.rnk + (size_t)gb * p.kp;
-    uint4* ul4 = reinterpret_cast<uint4*>(p.ulink + (size_t)gb * p.kp);
-    for (int w = 0; w < up.nw; ++w) W0[w * 32] = 0;
-    for (int s = 0; s < up.ns; ++s) W1[s * 32] = 0;
-    const uint32_t sentB = (uint32_t)k + 1;
-    const uint4* rk4 = reinterpret_cast<const uint4*>(rnk);
-    uint4 rv = __ldg(rk4);
-    uint4 rn = (NB > 8) ? __ldg(rk4 + 1) : rv;
-    uint32_t uo[4];
-    for (int i = 0; i < NB; ++i) {
-        if ((i & 7) == 0 && i > 0) {
-            rv = rn;
-            if (i + 8 < NB) rn = __ldg(rk4 + (i >> 3) + 1);
+    const int64_t gb = 1 + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * BPW + bslot;
+    uint32_t* ws = reinterpret_cast<uint32_t*>(smem) + warp * up.words_per_warp;
+    uint32_t* W0 = ws + lane;                                   // bitset word x at W0[x * 32]
+    uint32_t* W1 = ws + up.nw * 32 + lane;                      // summary words (when !SMALL)
+    uint32_t* PMW = ws + (up.nw + up.ns) * 32 + bslot;          // perm word x at PMW[x * BPW]
+    const bool live = gb < p.nblocks;
+    const int NB = live ? (int)min((int64_t)k, p.n - gb * (int64_t)k) : 0;
+    const uint16_t* perm = p.perm + (live ? gb : 0) * (int64_t)p.kp;
+    const uint16_t* rnk = p.rnk + (live ? gb : 0) * (int64_t)p.kp;
+    // ---- the block's perm into shared memory, split over its S lanes -------
+    {
+        const uint4* pm4 = reinterpret_cast<const uint4*>(perm);
+        const int nch = (NB + 7) >> 3;
+        for (int c = sg; c < nch; c += S) {
+            const uint4 v = __ldg(pm4 + c);
+            PMW[(4 * c + 0) * BPW] = v.x;
+            PMW[(4 * c + 1) * BPW] = v.y;
+            PMW[(4 * c + 2) * BPW] = v.z;
+            PMW[(4 * c + 3) * BPW] = v.w;
         }
-        const uint32_t rw = (i & 6) == 0 ? rv.x : (i & 6) == 2 ? rv.y : (i & 6) == 4 ? rv.z : rv.w;
-        const int r = (int)((i & 1) ? rw >> 16 : rw & 0xffffu);
-        const int w = r >> 5, b = r & 31;
-        const uint32_t word = W0[w * 32];
-        int pred = -1, succ = -1;
-        uint32_t m = word & ((1u << b) - 1u);
-        if (m) {
-            pred = (w << 5) | (31 - __clz(m));
-        } else {
-            int s = w >> 5;
-            uint32_t sm = W1[s * 32] & ((1u << (w & 31)) - 1u);
-            while (true) {
-                if (sm) {
-                    const int ww = (s << 5) | (31 - __clz(sm));
-                    pred = (ww << 5) | (31 - __clz(W0[ww * 32]));
-                    break;
-                }
-                if (--s < 0) break;
-                sm = W1[s * 32];
-            }
-        }
-        m = b == 31 ? 0u : (word & ~((2u << b) - 1u));
-        if (m) {
-            succ = (w << 5) | (__ffs(m) - 1);
-        } else {
-            int s = w >> 5;
-            const int wb = w & 31;
-            uint32_t sm = wb == 31 ? 0u : (W1[s * 32] & ~((2u << wb) - 1u));
-            while (true) {
-                if (sm) {
-                    const int ww = (s << 5) | (__ffs(sm) - 1);
-                    succ = (ww << 5) | (__ffs(W0[ww * 32]) - 1);
-                    break;
-                }
-                if (++s >= up.ns) break;
-                sm = W1[s * 32];
-            }
-        }
-        W0[w * 32] = word | (1u << b);
-        W1[(w >> 5) * 32] |= 1u << (w & 31);
-        const uint32_t pv = pred >= 0 ? (uint32_t)__ldg(perm + pred) : sentB;
-        const uint32_t nx = succ >= 0 ? (uint32_t)__ldg(perm + succ) : sentB;
-        uo[i & 3] = (pv << 16) | nx;
-        if ((i & 3) == 3) ul4[i >> 2] = make_uint4(uo[0], uo[1], uo[2], uo[3]);
     }
-    if (NB & 3) {                                   // flush the partial last group
-        for (int t = NB & 3; t < 4; ++t) uo[t] = 0;
-        ul4[(NB - 1) >> 2] = make_uint4(uo[0], uo[1], uo[2], uo[3]);
+    __syncwarp();
+    const int i0 = sg * up.seglen;
+    const int i1 = min(i0 + up.seglen, NB);
+    if (i0 >= i1) return;
+    for (int w = 0; w < up.nw; ++w) W0[w * 32] = 0;
+    if (!SMALL) for (int s = 0; s < up.ns; ++s) W1[s * 32] = 0;
+    const uint4* rk4 = reinterpret_cast<const uint4*>(rnk);
+    uint32_t summ = 0;                                          // SMALL: non-empty words
+    // ---- seed: ranks of positions 0 .. i0-1 (independent updates) ----------
+    for (int c = 0; c < (i0 >> 3); ++c) {
+        const uint4 v = __ldg(rk4 + c);
+        const uint32_t rw[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t r = (t & 1) ? rw[t >> 1] >> 16 : rw[t >> 1] & 0xffffu;
+            atomicOr(&W0[(r >> 5) * 32], 1u << (r & 31));
+            if (SMALL) summ |= 1u << (r >> 5);
+            else atomicOr(&W1[(r >> 10) * 32], 1u << ((r >> 5) & 31));
+        }
+    }
+    const uint32_t sentB = (uint32_t)k + 1;
+    uint4* ul4 = reinterpret_cast<uint4*>(p.ulink + gb * (int64_t)p.kp);
+    // ---- the run, 8 positions per round (rank chunk prefetched one ahead) ---
+    uint4 rn = __ldg(rk4 + (i0 >> 3));
+    for (int c0 = i0; c0 < i1; c0 += 8) {
+        const uint4 rv = rn;
+        if (c0 + 8 < i1) rn = __ldg(rk4 + (c0 >> 3) + 1);
+        const uint32_t rw[4] = {rv.x, rv.y, rv.z, rv.w};
+        uint32_t uo[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            uo[t] = 0u;
+            if (c0 + t < i1) {
+                const int r = (int)((t & 1) ? rw[t >> 1] >> 16 : rw[t >> 1] & 0xffffu);
+                const int w = r >> 5, b = r & 31;
+                const uint32_t word = W0[w * 32];
+                const uint32_t mlo = word & ((1u << b) - 1u);
+                const uint32_t mhi = word & ~((2u << b) - 1u);   // b = 31: 2u << 31 == 0, ~(0 - 1) == 0
+                int pred = -1, succ = -1;
+                if (SMALL) {
+                    const uint32_t slo = summ & ((1u << w) - 1u);
+                    const uint32_t shi = summ & ~((2u << w) - 1u);
+                    const int wlo = slo ? 31 - __clz(slo) : 0;
+                    const int whi = shi ? __ffs(shi) - 1 : 0;
+                    const uint32_t xlo = W0[wlo * 32], xhi = W0[whi * 32];
+                    pred = mlo ? ((w << 5) | (31 - __clz(mlo))) : (slo ? ((wlo << 5) | (31 - __clz(xlo))) : -1);
+                    succ = mhi ? ((w << 5) | (__ffs(mhi) - 1)) : (shi ? ((whi << 5) | (__ffs(xhi) - 1)) : -1);
+                    summ |= 1u << w;
+                } else {
+                    if (mlo) {
+                        pred = (w << 5) | (31 - __clz(mlo));
+                    } else {
+                        int s = w >> 5;
+                        uint32_t sm = W1[s * 32] & ((1u << (w & 31)) - 1u);
+                        while (true) {
+                            if (sm) {
+                                const int ww = (s << 5) | (31 - __clz(sm));
+                                pred = (ww << 5) | (31 - __clz(W0[ww * 32]));
+                                break;
+                            }
+                            if (--s < 0) break;
+                            sm = W1[s * 32];
+                        }
+                    }
+                    if (mhi) {
+                        succ = (w << 5) | (__ffs(mhi) - 1);
+                    } else {
+                        int s = w >> 5;
+                        uint32_t sm = W1[s * 32] & ~((2u << (w & 31)) - 1u);
+                        while (true) {
+                            if (sm) {
+                                const int ww = (s << 5) | (__ffs(sm) - 1);
+                                succ = (ww << 5) | (__ffs(W0[ww * 32]) - 1);
+                                break;
+                            }
+                            if (++s >= up.ns) break;
+                            sm = W1[s * 32];
+                        }
+                    }
+                    W1[(w >> 5) * 32] |= 1u << (w & 31);
+                }
+                W0[w * 32] = word | (1u << b);
+                uint32_t pv = sentB, nx = sentB;
+                if (pred >= 0) { const uint32_t pw = PMW[(pred >> 1) * BPW]; pv = (pred & 1) ? pw >> 16 : pw & 0xffffu; }
+                if (succ >= 0) { const uint32_t nw2 = PMW[(succ >> 1) * BPW]; nx = (succ & 1) ? nw2 >> 16 : nw2 & 0xffffu; }
+                uo[t] = (pv << 16) | nx;
+            }
+        }
+        // runs start on multiples of 8, so these two 16-byte groups are ours
+        ul4[c0 >> 2] = make_uint4(uo[0], uo[1], uo[2], uo[3]);
+        if (c0 + 4 < i1) ul4[(c0 >> 2) + 1] = make_uint4(uo[4], uo[5], uo[6], uo[7]);
     }
 }
 
@@ -224,20 +273,30 @@ unwind_kernel(PipeParams p, UnwindPlan up)
 //   wide             : next:16 | prev:16, joint rank in a separate u16 array
 // Relinks never read the word: when delete(A, i) unlinks i, next(prev(i)) is
 // i and prev(next(i)) is i; when undelete(B, i) relinks i between p and n,
-// next(p) is n and prev(n) is p.  So each relink is one XOR of old ^ new into
-// the field (equations del / undo-del of Section 3).
+// next(p) is n and prev(n) is p.  So in the packed format each relink is one
+// XOR of old ^ new into the field; in the wide format it is a 16-bit store
+// (equations del / undo-del of Section 3).
 template <bool PACKED>
 struct Lists {
     static constexpr int PSH = PACKED ? 10 : 16;
     static constexpr uint32_t FM = PACKED ? 0x3ffu : 0xffffu;
     static constexpr uint32_t RINF = PACKED ? 0x7ffu : 0xffffu;
-    uint32_t* w;
-    uint16_t* jr16;
-    int NL;
-    __device__ __forceinline__ uint32_t ld(uint32_t e) const { return w[(size_t)e * NL]; }
-    __device__ __forceinline__ void st(uint32_t e, uint32_t v) const { w[(size_t)e * NL] = v; }
-    __device__ __forceinline__ void xr(uint32_t e, uint32_t v) const { atomicXor(&w[(size_t)e * NL], v); }
-    __device__ __forceinline__ uint16_t& JR(uint32_t e) const { return jr16[(size_t)(e >> 1) * 2 * NL + (e & 1)]; }
+    uint32_t* w;              // this lane's word 0
+    uint16_t* jr16;           // wide format: this lane's rank array
+    uint32_t NL;              // lanes of this warp: slot e's word is w[e * NL]
+    __device__ __forceinline__ uint32_t ld(uint32_t e) const { return w[e * NL]; }
+    __device__ __forceinline__ void st(uint32_t e, uint32_t v) const { w[e * NL] = v; }
+    __device__ __forceinline__ void xr(uint32_t e, uint32_t v) const { atomicXor(&w[e * NL], v); }
+    // relinks: next(e) <- v (old value `old`), prev(e) <- v
+    __device__ __forceinline__ void set_next(uint32_t e, uint32_t v, uint32_t old) const {
+        if (PACKED) xr(e, v ^ old);
+        else reinterpret_cast<uint16_t*>(w)[e * 2 * NL] = (uint16_t)v;
+    }
+    __device__ __forceinline__ void set_prev(uint32_t e, uint32_t v, uint32_t old) const {
+        if (PACKED) xr(e, (v ^ old) << PSH);
+        else reinterpret_cast<uint16_t*>(w)[e * 2 * NL + 1] = (uint16_t)v;
+    }
+    __device__ __forceinline__ uint16_t& JR(uint32_t e) const { return jr16[(e >> 1) * 2 * NL + (e & 1)]; }
     __device__ __forceinline__ static uint32_t nxt(uint32_t v) { return v & FM; }
     __device__ __forceinline__ static uint32_t prv(uint32_t v) { return (v >> PSH) & FM; }
     // rank of slot e whose word is v
@@ -271,8 +330,8 @@ __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>
     // -------- delete(A, i) ----------------------------------------------------
     const uint32_t pa = LL::prv(wa), na = LL::nxt(wa);
     const uint32_t ra = L.rank(i, wa);
-    L.xr(pa, i ^ na);                                   // next[prev[i]] <- next[i]
-    L.xr(na, (i ^ pa) << LL::PSH);                      // prev[next[i]] <- prev[i]
+    L.set_next(pa, na, i);                              // next[prev[i]] <- next[i]
+    L.set_prev(na, pa, i);                              // prev[next[i]] <- prev[i]
     st.wmA ^= (pa == st.mA) ? (i ^ na) : 0u;            // keep m's cached word exact
     st.wmA ^= (na == st.mA) ? ((i ^ pa) << LL::PSH) : 0u;
     if (PACKED) st.rmA = st.wmA >> 20;
@@ -293,8 +352,8 @@ __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>
     // -------- undelete(B, i) ----------------------------------------------------
     L.st(i, LL::make(pb, nb, rb));
     if (!PACKED) L.JR(i) = (uint16_t)rb;
-    L.xr(pb, nb ^ i);                                   // next[prev[i]] <- i
-    L.xr(nb, (pb ^ i) << LL::PSH);                      // prev[next[i]] <- i
+    L.set_next(pb, i, nb);                              // next[prev[i]] <- i
+    L.set_prev(nb, i, pb);                              // prev[next[i]] <- i
     st.wmB ^= (pb == st.mB) ? (nb ^ i) : 0u;
     st.wmB ^= (nb == st.mB) ? ((pb ^ i) << LL::PSH) : 0u;
     const bool smallB = rb < st.rmB;                    // small: m <- prev[m]
@@ -332,22 +391,15 @@ __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>
 }
 
 template <bool PACKED>
-__global__ void __launch_bounds__(kPipeThreads)
-chain_kernel(PipeParams p, ChainPlan cp)
+__device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, int lane, int64_t q,
+                                           uint32_t rec_words, uint32_t NL)
 {
     using LL = Lists<PACKED>;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int NL = cp.lanes[warp];
-    if (lane >= NL) return;
-    const int64_t q = (int64_t)blockIdx.x * cp.pairs_per_cta + cp.pair_off[warp] + lane;
-    if (q >= p.npairs) return;                          // pair j = q + 1
     const int k = p.k, h = p.h;
     const int NB = (int)min((int64_t)k, p.n - (q + 1) * (int64_t)k);
-    uint32_t* wsl = reinterpret_cast<uint32_t*>(smem) + cp.word_off[warp];
     LL L;
     L.w = wsl + lane;
-    L.jr16 = reinterpret_cast<uint16_t*>(wsl + (size_t)cp.rec_words * NL + lane);
+    L.jr16 = reinterpret_cast<uint16_t*>(wsl + rec_words * NL + lane);
     L.NL = NL;
 
     // ---- construct(A) in slot space + empty B (rows of kp elements) ----------
@@ -372,7 +424,7 @@ chain_kernel(PipeParams p, ChainPlan cp)
         }
     }
     const uint32_t SA = (uint32_t)k, SB = (uint32_t)k + 1;
-    const uint16_t* permA = p.perm + abase;
+    const uint16_t* permA = p.perm + abase;                     // block j-1 = q
     L.st(SA, LL::make(__ldg(permA + k - 1), __ldg(permA), LL::RINF));
     L.st(SB, LL::make(SB, SB, LL::RINF));
     if (!PACKED) { L.JR(SA) = (uint16_t)LL::RINF; L.JR(SB) = (uint16_t)LL::RINF; }
@@ -424,6 +476,25 @@ chain_kernel(PipeParams p, ChainPlan cp)
     }
 }
 
+template <bool PACKED>
+__global__ void __launch_bounds__(kPipeThreads)
+chain_kernel(PipeParams p, ChainPlan cp)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp w has 1 << ((lanes_log2 >> 3w) & 7) lanes; slices follow each other
+    int NL = 0, pair_off = 0;
+    for (int w = 0; w <= warp; ++w) {
+        const int l = 1 << ((cp.lanes_log2 >> (3 * w)) & 7);
+        if (w < warp) pair_off += l; else NL = l;
+    }
+    if (lane >= NL) return;
+    const int64_t q = (int64_t)blockIdx.x * cp.pairs_per_cta + pair_off + lane;
+    if (q >= p.npairs) return;                          // pair j = q + 1
+    uint32_t* wsl = reinterpret_cast<uint32_t*>(smem) + (uint32_t)pair_off * cp.lane_words;
+    chain_body<PACKED>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL);
+}
+
 // ===========================================================================
 // epilogue_kernel: y[(j-1)k + 1 + i] = the element printed at step i of pair
 // j, read from a shared-memory copy of the CTA's input span; y[0] = X_0[P_0[h]].
@@ -445,13 +516,27 @@ epilogue_kernel(PipeParams p, int G)
     const int nout = npair > 0 ? E - k : 0;
     uint32_t* ys = p.y + ebase + 1;
     int32_t* as = p.argmed ? p.argmed + ebase + 1 : nullptr;
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-        const int g = o / k;
-        const int i = o - g * k;
-        const uint32_t id = p.out[(size_t)(j0 - 1 + g) * p.kp + i];
-        const int e = (g + (int)(id >> 15)) * k + (int)(id & 0x7fffu);
-        ys[o] = xs[e];
-        if (as) as[o] = (int32_t)(ebase + e);
+    const uint16_t* outs = p.out + (size_t)(j0 - 1) * p.kp;
+    const int stride = blockDim.x;
+    // four outputs per thread per round: loads first, then lookups and stores
+    for (int o0 = threadIdx.x; o0 < nout; o0 += 4 * stride) {
+        uint32_t id[4];
+        int g[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int o = o0 + u * stride;
+            g[u] = o / k;
+            id[u] = o < nout ? (uint32_t)outs[(size_t)g[u] * p.kp + (o - g[u] * k)] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int o = o0 + u * stride;
+            if (o < nout) {
+                const int e = (g[u] + (int)(id[u] >> 15)) * k + (int)(id[u] & 0x7fffu);
+                ys[o] = xs[e];
+                if (as) as[o] = (int32_t)(ebase + e);
+            }
+        }
     }
     if (j0 == 1 && threadIdx.x == 0) {
         const int pm = p.perm[p.h];
@@ -489,20 +574,20 @@ static bool chain_plan(int k, ChainPlan* cp, size_t* bytes)
     cp->packed = k <= 1021;
     cp->rec_words = (uint32_t)(k + 2);
     const uint32_t lane_words = cp->rec_words + (cp->packed ? 0u : (uint32_t)((k + 3) / 2));
+    cp->lane_words = lane_words;
     const uint64_t budget = (uint64_t)kMaxSmemBytes / 4;       // words
     uint64_t used = 0;
     int nw = 0, pairs = 0;
+    cp->lanes_log2 = 0;
     while (nw < kPipeThreads / 32) {
-        int lanes = 32;
-        while (lanes > 0 && used + (uint64_t)lanes * lane_words > budget) lanes >>= 1;
-        if (lanes == 0) break;
-        cp->lanes[nw] = lanes;
-        cp->word_off[nw] = (uint32_t)used;
-        cp->pair_off[nw] = pairs;
-        used += (uint64_t)lanes * lane_words;
-        pairs += lanes;
+        int lg = 5;
+        while (lg >= 0 && used + ((uint64_t)1 << lg) * lane_words > budget) --lg;
+        if (lg < 0) break;
+        cp->lanes_log2 |= (uint32_t)lg << (3 * nw);
+        used += ((uint64_t)1 << lg) * lane_words;
+        pairs += 1 << lg;
         ++nw;
-        if (lanes < 32 && lanes == 1) break;
+        if (lg == 0) break;
     }
     cp->nwarps = nw;
     cp->pairs_per_cta = pairs;
@@ -544,7 +629,8 @@ cudaError_t pipeline_setup()
 {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(sortmerge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
-    if ((e = cudaFuncSetAttribute(unwind_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(unwind_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(unwind_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
     if ((e = cudaFuncSetAttribute(chain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
     if ((e = cudaFuncSetAttribute(chain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
     return cudaFuncSetAttribute(epilogue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
@@ -552,8 +638,16 @@ cudaError_t pipeline_setup()
 
 cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, bool is_float,
                             uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes,
-                            int num_sms, cudaStream_t stream, uint64_t* launches)
+                            int num_sms, cudaStream_t stream, LaunchStats* stats)
 {
+    // optional timing: events before each kernel and after the last one, in
+    // the next slot of the handle's ring
+    cudaEvent_t* evs = nullptr;
+    if (stats && stats->timing) {
+        evs = stats->ev[stats->ring_pos % LaunchStats::kRing];
+        stats->ring_pos += 1;
+    }
+#define TIMER_MARK(idx) do { if (evs) cudaEventRecord(evs[idx], stream); } while (0)
     if (ws_bytes < pipeline_workspace_bytes(n, k)) return cudaErrorInvalidValue;
     PipeParams p{};
     p.x = x; p.y = y; p.argmed = argmed;
@@ -594,27 +688,33 @@ cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, bool is_float,
     if (cap > 255) cap = 255;
     sp.bpg = max(1, min(bpg, cap));
     const int64_t sgrid = p.npairs > 0 ? (p.npairs + G - 1) / G : 1;
+    TIMER_MARK(0);
     sortmerge_kernel<<<(unsigned)sgrid, kPipeThreads, sbytes, stream>>>(p, sp);
-    if (launches) *launches += 1;
+    if (stats) stats->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
     if (p.npairs > 0) {
-        // ---- unwind: one lane per block 1 .. b-1 ---------------------------
+        // ---- unwind: lanes = (block, run) pairs --------------------------------
         UnwindPlan up{};
         up.nw = (k + 31) / 32;
-        up.ns = (up.nw + 31) / 32;
-        up.lanes = 32;
-        up.words_per_warp = (uint32_t)((up.nw + up.ns) * 32);
+        up.ns = up.nw <= 32 ? 0 : (up.nw + 31) / 32;
+        up.segs = k >= 256 ? 4 : (k >= 64 ? 2 : 1);
+        up.seglen = (((k + up.segs - 1) / up.segs) + 7) & ~7;
+        const int bpw = 32 / up.segs;
+        up.words_per_warp = (uint32_t)((up.nw + up.ns) * 32) + (uint32_t)(p.kp / 2) * (uint32_t)bpw;
         int uw = W;
-        while (uw > 1 && (size_t)up.words_per_warp * 4 * uw > (size_t)kMaxSmemBytes / 4) --uw;
+        while (uw > 1 && (size_t)up.words_per_warp * 4 * uw > (size_t)kMaxSmemBytes / 2) --uw;
         const size_t ubytes = (size_t)up.words_per_warp * 4 * uw;
         if (ubytes > (size_t)kMaxSmemBytes) return cudaErrorInvalidValue;
-        const int64_t nb1 = p.nblocks - 1;
-        const int64_t per_ucta = (int64_t)uw * 32;
-        const int64_t ugrid = (nb1 + per_ucta - 1) / per_ucta;
-        unwind_kernel<<<(unsigned)ugrid, 32 * uw, ubytes, stream>>>(p, up);
-        if (launches) *launches += 1;
+        const int64_t per_ucta = (int64_t)uw * bpw;
+        const int64_t ugrid = (p.nblocks - 1 + per_ucta - 1) / per_ucta;
+        TIMER_MARK(1);
+        if (up.ns == 0)
+            unwind_kernel<true><<<(unsigned)ugrid, 32 * uw, ubytes, stream>>>(p, up);
+        else
+            unwind_kernel<false><<<(unsigned)ugrid, 32 * uw, ubytes, stream>>>(p, up);
+        if (stats) stats->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
         // ---- chain ----------------------------------------------------------
@@ -622,20 +722,27 @@ cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, bool is_float,
         size_t cbytes = 0;
         if (!chain_plan(k, &cp, &cbytes)) return cudaErrorInvalidValue;
         const int64_t cgrid = (p.npairs + cp.pairs_per_cta - 1) / cp.pairs_per_cta;
+        TIMER_MARK(2);
         if (cp.packed)
             chain_kernel<true><<<(unsigned)cgrid, 32 * cp.nwarps, cbytes, stream>>>(p, cp);
         else
             chain_kernel<false><<<(unsigned)cgrid, 32 * cp.nwarps, cbytes, stream>>>(p, cp);
-        if (launches) *launches += 1;
+        if (stats) stats->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        TIMER_MARK(1);
+        TIMER_MARK(2);
     }
 
     // ---- epilogue -----------------------------------------------------------
     int GE = max(1, min(16, 8192 / k));
     const size_t ebytes = 4ull * (size_t)(GE + 1) * k;
     const int64_t egrid = p.npairs > 0 ? (p.npairs + GE - 1) / GE : 1;
+    TIMER_MARK(3);
     epilogue_kernel<<<(unsigned)egrid, kPipeThreads, ebytes, stream>>>(p, GE);
-    if (launches) *launches += 1;
+    if (stats) stats->launches += 1;
+    TIMER_MARK(4);
+#undef TIMER_MARK
     return cudaGetLastError();
 }
 
