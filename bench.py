@@ -83,6 +83,17 @@ def reduce_max(dist, value, dev=None):
     return float(t.item())
 
 
+def weak_scaling_value(world_size, outputs_per_rank, steps, max_ms):
+    """Whole-job throughput in Gsamples/s: every rank filters its own signal,
+    so the job's outputs over the slowest rank's time."""
+    return world_size * outputs_per_rank * steps / (max_ms * 1e-3) / 1e9
+
+
+def rank_seed(base_seed, rank):
+    """Each rank filters an independent signal drawn with base_seed + rank."""
+    return base_seed + rank
+
+
 # ---------------------------------------------------------------------------
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -242,7 +253,7 @@ def run_ours(args):
         import __graft_entry__
         __graft_entry__.build()
     from signals import DEFAULT_SEED
-    seed = DEFAULT_SEED + rank
+    seed = rank_seed(DEFAULT_SEED, rank)
 
     stream = torch.cuda.Stream(dev)
     h = mf.mf_create(dev.index, stream)
@@ -287,12 +298,12 @@ def run_ours(args):
     clocks = sampler.stop(*win)
     total_ms_max = reduce_max(dist, total_ms, dev)
     ms_per_step = total_ms_max / args.steps
-    value = ws * m * args.steps / (total_ms_max * 1e-3) / 1e9
+    value = weak_scaling_value(ws, m, args.steps, total_ms_max)
 
     # int32 uniform variant of the same size (random-input case)
     _, total_i, per_i, _, _, kt_i = device_run("int")
     total_i = reduce_max(dist, total_i, dev)
-    value_int = ws * m * args.steps / (total_i * 1e-3) / 1e9
+    value_int = weak_scaling_value(ws, m, args.steps, total_i)
 
     # end to end through the host-buffer entry point (pinned host memory)
     xh = torch.from_numpy(x_walk).pin_memory()

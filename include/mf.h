@@ -113,9 +113,16 @@ mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_
 /* Filter many independent signals in one call (all of one dtype).
  *  x, y       device base pointers; signal s is x[segs[s].x_off ..+n) and
  *             writes y[segs[s].y_off ..+ n-k+1)
- *  segs_host  HOST array of nseg descriptors (copied before return)
+ *  segs_host  HOST array of nseg descriptors (read before return)
  *  argmed     device pointer parallel to y (index within each signal) or NULL
  * Output ranges must not overlap each other or x.
+ * The signals are grouped by window size into at most six classes and each
+ * class runs as one launch per kernel (at most 24 launches per call,
+ * whatever nseg is).  The call can be captured into a CUDA graph: make one
+ * uncaptured call with the same sizes first (it allocates the workspace and
+ * a pinned descriptor buffer; during capture nothing may be allocated and
+ * such calls return MF_ERR_OOM).  A captured call's descriptors stay with
+ * its graph; later calls on the handle use a new buffer.
  * Errors: as mf_filter, plus MF_ERR_BAD_SEGMENT (naming no segment index:
  * any invalid descriptor rejects the whole call), MF_ERR_OOM. */
 mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
@@ -163,6 +170,14 @@ mf_status mf_sync(mf_handle h);
 
 /* Number of kernels this handle has launched since creation (for accounting). */
 mf_status mf_launch_count(mf_handle h, uint64_t* count);
+
+/* Launch-plan tuning for the window-size class that contains k (classes
+ * k <= 64, <= 256, <= 1021, <= 2047, <= 4095, larger): block pairs per CTA
+ * of the sort+merge kernel and of the store kernel (0 = built-in choice;
+ * values above the built-in choice, which fills shared memory, are capped).
+ * Used by the autotuner in paper_1406_1717_gb300/tune.py. */
+mf_status mf_set_tuning(mf_handle h, int32_t k, int32_t sort_pairs_per_cta,
+                        int32_t store_pairs_per_cta);
 
 /* Per-kernel timing for measurement.  With timing enabled, every mf_filter /
  * mf_filter_host call records CUDA events on the handle's stream around its

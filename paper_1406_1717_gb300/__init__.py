@@ -10,7 +10,7 @@ fallback: if the library is missing, every call raises.
 
 Functions carry the C names: ``mf_create``, ``mf_set_stream``, ``mf_filter``,
 ``mf_filter_host``, ``mf_filter_batched``, ``mf_filter_backward``,
-``mf_filter_noalloc``, ``mf_sync``, ``mf_launch_count``, ``mf_set_timing``,
+``mf_filter_noalloc``, ``mf_sync``, ``mf_launch_count``, ``mf_set_tuning``, ``mf_set_timing``,
 ``mf_kernel_times``, ``mf_status_str``, ``mf_destroy``.
 ``median_filter`` is a convenience wrapper that allocates the outputs.
 """
@@ -72,6 +72,7 @@ def load_library(path: str = LIB_PATH):
             "mf_sync": ([vp], c.c_int),
             "mf_launch_count": ([vp, c.POINTER(c.c_uint64)], c.c_int),
             "mf_set_timing": ([vp, c.c_int], c.c_int),
+            "mf_set_tuning": ([vp, i32, i32, i32], c.c_int),
             "mf_kernel_times": ([vp, i32, c.POINTER(c.c_float)], c.c_int),
             "mf_status_str": ([c.c_int], c.c_char_p),
             "mf_destroy": ([vp], c.c_int),
@@ -205,6 +206,12 @@ def mf_launch_count(handle) -> int:
 
 
 KERNEL_NAMES = ("sortmerge", "unwind", "chain", "epilogue")
+
+
+def mf_set_tuning(handle, k: int, sort_pairs_per_cta: int = 0, store_pairs_per_cta: int = 0):
+    """Launch-plan choice for the window-size class containing k (0 = built-in)."""
+    _check(load_library().mf_set_tuning(handle, int(k), int(sort_pairs_per_cta),
+                                        int(store_pairs_per_cta)), "mf_set_tuning")
 
 
 def mf_set_timing(handle, enable: bool = True):

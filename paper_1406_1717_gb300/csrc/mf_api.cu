@@ -22,6 +22,14 @@ struct mf_ctx {
     int max_k;
     mf::LaunchStats stats;
     bool events_made;
+    mf::Tuning tune[mf::kNumTuneClasses];
+    // pinned staging of batched descriptor tables; a buffer that a captured
+    // call used belongs to that graph and is kept until mf_destroy
+    void* stage;
+    size_t stage_size;
+    bool stage_in_graph;
+    cudaEvent_t stage_done;
+    std::vector<void*> retired;
 };
 
 namespace {
@@ -52,9 +60,16 @@ mf_status check_common(mf_handle h, int dtype, const void* x, int64_t n, int32_t
     return MF_OK;
 }
 
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) { cudaGetLastError(); return false; }
+    return st == cudaStreamCaptureStatusActive;
+}
+
 mf_status ensure_workspace(mf_handle h, size_t bytes) {
     if (h->ws_size >= bytes) return MF_OK;
     if (h->max_ws && bytes > h->max_ws) return MF_ERR_OOM;
+    if (capturing(h->stream)) return MF_ERR_OOM;      // allocate before capturing
     if (h->ws) {
         cudaStreamSynchronize(h->stream);
         cudaFree(h->ws);
@@ -97,6 +112,15 @@ mf_status mf_create(mf_handle* out, int device, void* cuda_stream, size_t max_wo
     h->num_sms = prop.multiProcessorCount;
     h->max_k = mf::pipeline_max_k();
     h->events_made = false;
+    for (int c = 0; c < mf::kNumTuneClasses; ++c) h->tune[c] = mf::Tuning{0, 0};
+    h->stats.tune = h->tune;
+    h->stage = nullptr;
+    h->stage_size = 0;
+    h->stage_in_graph = false;
+    if (cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+        delete h;
+        return MF_ERR_CUDA;
+    }
     *out = h;
     return MF_OK;
 }
@@ -186,20 +210,43 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
         return MF_ERR_OVERLAP;
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
-    size_t need = 0;
-    for (int32_t s = 0; s < nseg; ++s)
-        need = std::max(need, mf::pipeline_workspace_bytes(segs[s].n, segs[s].k));
+    if (nseg == 0) return MF_OK;
+    std::vector<int64_t> xo((size_t)nseg), nn((size_t)nseg), yo((size_t)nseg);
+    std::vector<int32_t> kk((size_t)nseg);
+    for (int32_t s = 0; s < nseg; ++s) {
+        xo[s] = segs[s].x_off; nn[s] = segs[s].n; yo[s] = segs[s].y_off; kk[s] = segs[s].k;
+    }
+    const size_t need = mf::pipeline_batched_workspace_bytes(nn.data(), kk.data(), nseg);
     mf_status st = ensure_workspace(h, need);
     if (st != MF_OK) return st;
-    const uint32_t* xb = (const uint32_t*)x;
-    uint32_t* yb = (uint32_t*)y;
-    for (int32_t s = 0; s < nseg; ++s) {
-        const mf_segment& d = segs[s];
-        cudaError_t e = mf::launch_pipeline(xb + d.x_off, d.n, d.k, dtype == MF_FLOAT32,
-                                            yb + d.y_off, argmed ? argmed + d.y_off : nullptr,
-                                            h->ws, need, h->num_sms, h->stream, &h->stats);
-        if (e != cudaSuccess) return MF_ERR_CUDA;
+    const size_t stage_need = (size_t)nseg * sizeof(mf::PipeParams);
+    const bool cap = capturing(h->stream);
+    if (!cap) {
+        if (h->stage_in_graph) {                      // leave that buffer to its graph
+            h->retired.push_back(h->stage);
+            h->stage = nullptr;
+            h->stage_size = 0;
+            h->stage_in_graph = false;
+        } else if (h->stage) {
+            cudaEventSynchronize(h->stage_done);      // previous copy has read the buffer
+        }
+        if (h->stage_size < stage_need) {
+            if (h->stage) cudaFreeHost(h->stage);
+            h->stage = nullptr;
+            h->stage_size = 0;
+            if (cudaMallocHost(&h->stage, stage_need) != cudaSuccess) { cudaGetLastError(); return MF_ERR_OOM; }
+            h->stage_size = stage_need;
+        }
+    } else if (h->stage_size < stage_need || h->stage_in_graph) {
+        return MF_ERR_OOM;                            // make one uncaptured call of this size first
     }
+    cudaError_t e = mf::launch_pipeline_batched((const uint32_t*)x, (uint32_t*)y, argmed,
+                                                dtype == MF_FLOAT32, xo.data(), nn.data(), yo.data(),
+                                                kk.data(), nseg, h->ws, need, h->stage, h->stage_size,
+                                                h->num_sms, h->stream, &h->stats);
+    if (e != cudaSuccess) return MF_ERR_CUDA;
+    if (cap) h->stage_in_graph = true;
+    else cudaEventRecord(h->stage_done, h->stream);
     return MF_OK;
 }
 
@@ -230,6 +277,15 @@ mf_status mf_sync(mf_handle h) {
 mf_status mf_launch_count(mf_handle h, uint64_t* count) {
     if (!h || !count) return MF_ERR_NULL;
     *count = h->stats.launches;
+    return MF_OK;
+}
+
+mf_status mf_set_tuning(mf_handle h, int32_t k, int32_t sort_pairs_per_cta, int32_t store_pairs_per_cta) {
+    if (!h) return MF_ERR_NULL;
+    if (k < 1) return MF_ERR_K_GT_N;
+    mf::Tuning& t = h->tune[mf::tune_class_of(k)];
+    t.sort_G = sort_pairs_per_cta > 0 ? sort_pairs_per_cta : 0;
+    t.epi_G = store_pairs_per_cta > 0 ? store_pairs_per_cta : 0;
     return MF_OK;
 }
 
@@ -299,6 +355,9 @@ mf_status mf_destroy(mf_handle h) {
             if (h->events_made)
                 for (int r = 0; r < mf::LaunchStats::kRing; ++r)
                     for (int j = 0; j < 5; ++j) cudaEventDestroy(h->stats.ev[r][j]);
+            cudaEventDestroy(h->stage_done);
+            if (h->stage) cudaFreeHost(h->stage);
+            for (void* r : h->retired) cudaFreeHost(r);
         }
     }
     delete h;

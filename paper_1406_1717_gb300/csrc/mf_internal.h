@@ -25,15 +25,31 @@ struct PipeParams {
     uint16_t* ja;             // [npairs][kp] joint rank of A's position p
     uint16_t* jb;             // [npairs][kp] joint rank of B's position p
     uint16_t* out;            // [npairs][kp] printed node at step i: isB << 15 | slot
+    int64_t start[4];         // batched launches: this signal's first item per kernel
+};
+
+// The signals of one launch: one descriptor by value, or a device table
+// (segs != nullptr) sorted by first item.
+struct SegTable {
+    const PipeParams* segs;
+    int nseg;
+    PipeParams one;
+};
+
+// Optional per-handle tuning of the launch plans (0 = built-in choice).
+struct Tuning {
+    int sort_G;               // pairs per sortmerge CTA
+    int epi_G;                // pairs per epilogue CTA
 };
 struct SortPlan {
     uint32_t off_keyA, off_keyB, off_valA, off_valB, off_hist;
-    int G, bpg;
+    int G;
 };
 struct UnwindPlan {
     int segs, seglen;         // runs per block (1, 2, 4) and positions per run (multiple of 8)
     int nw, ns;               // bitset words; summary words (0: one summary word in a register)
     uint32_t words_per_warp;
+    int64_t items;            // warp groups in the launch
 };
 struct ChainPlan {
     bool packed;              // one 32-bit word per list node (k <= 1021)
@@ -42,6 +58,7 @@ struct ChainPlan {
     uint32_t lanes_log2;      // 3 bits per warp: warp w handles 1 << field pairs
     uint32_t lane_words;      // shared-memory words per pair
     uint32_t rec_words;       // k + 2
+    int64_t items;            // pairs in the launch
 };
 
 // Launch accounting of a handle: kernel count and, when timing is on, CUDA
@@ -52,7 +69,11 @@ struct LaunchStats {
     bool timing = false;
     uint64_t ring_pos = 0;
     cudaEvent_t ev[kRing][5];
+    const Tuning* tune = nullptr;      // per launch class, kNumTuneClasses entries
 };
+
+constexpr int kNumTuneClasses = 6;     // classes of k: <= 64, 256, 1021, 2047, 4095, larger
+int tune_class_of(int k);
 
 int pipeline_max_k();
 size_t pipeline_workspace_bytes(int64_t n, int k);
@@ -60,6 +81,14 @@ cudaError_t pipeline_setup();
 cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, bool is_float,
                             uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes,
                             int num_sms, cudaStream_t stream, LaunchStats* stats);
+size_t pipeline_batched_workspace_bytes(const int64_t* n, const int32_t* k, int nseg);
+// Batched: `stage` is host memory (pinned for graph capture) of at least
+// nseg * sizeof(PipeParams) bytes that must stay unchanged until the copy ran.
+cudaError_t launch_pipeline_batched(const uint32_t* x, uint32_t* y, int32_t* argmed, bool is_float,
+                                    const int64_t* x_off, const int64_t* n, const int64_t* y_off,
+                                    const int32_t* k, int nseg, void* ws, size_t ws_bytes,
+                                    void* stage, size_t stage_bytes, int num_sms,
+                                    cudaStream_t stream, LaunchStats* stats);
 
 cudaError_t backward_setup();
 cudaError_t launch_backward(const float* gy, const int32_t* argmed, int64_t n, int k,

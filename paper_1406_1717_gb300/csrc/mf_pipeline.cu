@@ -37,11 +37,37 @@ namespace mf {
 
 
 // ===========================================================================
+// Signals and work items.  Every kernel works on items (sortmerge and
+// epilogue: CTAs of G consecutive block pairs; unwind: warp groups of blocks;
+// chain: block pairs).  A launch covers one signal (descriptor passed by
+// value) or a batch of signals (device table; each descriptor carries the
+// index of its first item in every kernel, and an item finds its signal by
+// binary search).
+// ===========================================================================
+enum { kItemSort = 0, kItemUnwind = 1, kItemChain = 2, kItemEpilogue = 3 };
+
+__device__ __forceinline__ PipeParams find_signal(const SegTable& t, int kern, int64_t item,
+                                                  int64_t* local)
+{
+    if (t.segs == nullptr) { *local = item; return t.one; }
+    int lo = 0, hi = t.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.segs[mid].start[kern] <= item) lo = mid; else hi = mid - 1;
+    }
+    const PipeParams p = t.segs[lo];
+    *local = item - p.start[kern];
+    return p;
+}
+
+// ===========================================================================
 // sortmerge_kernel
 // ===========================================================================
 __global__ void __launch_bounds__(kPipeThreads)
-sortmerge_kernel(PipeParams p, SortPlan sp)
+sortmerge_kernel(SegTable tab, SortPlan sp)
 {
+    int64_t cta;
+    const PipeParams p = find_signal(tab, kItemSort, blockIdx.x, &cta);
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* keyA = reinterpret_cast<uint32_t*>(smem + sp.off_keyA);
     uint32_t* keyB = reinterpret_cast<uint32_t*>(smem + sp.off_keyB);
@@ -52,13 +78,17 @@ sortmerge_kernel(PipeParams p, SortPlan sp)
     const int tid = threadIdx.x, warp = tid >> 5;
     const int W = blockDim.x >> 5;
     const int k = p.k;
-    const int64_t j0 = 1 + (int64_t)blockIdx.x * sp.G;
+    const int64_t j0 = 1 + cta * sp.G;
     const int64_t left = p.npairs - (j0 - 1);
     const int npair = (int)(left < sp.G ? (left > 0 ? left : 0) : sp.G);
     const int nblk = npair + 1;
     const int64_t ebase = (j0 - 1) * (int64_t)k;
     const int64_t rem = p.n - ebase;
     const int E = (int)((int64_t)nblk * k < rem ? (int64_t)nblk * k : rem);
+    // blocks sorted per warp: enough blocks for all warps, at most ~2048 elements
+    int bpg = (nblk + W - 1) / W;
+    const int cap = min(255, max(1, 2048 / k));
+    bpg = max(1, min(bpg, cap));
 
     for (int e = tid; e < E; e += blockDim.x) {
         keyA[e] = to_key(__ldg(p.x + ebase + e), p.is_float);
@@ -66,10 +96,10 @@ sortmerge_kernel(PipeParams p, SortPlan sp)
     }
     __syncthreads();
 
-    const int ngroups = (nblk + sp.bpg - 1) / sp.bpg;
+    const int ngroups = (nblk + bpg - 1) / bpg;
     for (int gi = warp; gi < ngroups; gi += W) {
-        const int b0 = gi * sp.bpg;
-        const int b1 = min(b0 + sp.bpg, nblk);
+        const int b0 = gi * bpg;
+        const int b1 = min(b0 + bpg, nblk);
         const int e0 = b0 * k;
         const int e1 = min(b1 * k, E);
         warp_sort_group(keyA + e0, valA + e0, keyB + e0, valB + e0,
@@ -136,14 +166,18 @@ sortmerge_kernel(PipeParams p, SortPlan sp)
 // ===========================================================================
 template <bool SMALL>
 __global__ void __launch_bounds__(kPipeThreads)
-unwind_kernel(PipeParams p, UnwindPlan up)
+unwind_kernel(SegTable tab, UnwindPlan up)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int S = up.segs, BPW = 32 / S;
     const int bslot = lane / S, sg = lane - bslot * S;
+    const int64_t wg = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;   // warp group
+    if (wg >= up.items) return;                                           // warp-uniform
+    int64_t lwg;
+    const PipeParams p = find_signal(tab, kItemUnwind, wg, &lwg);
     const int k = p.k;
-    const int64_t gb = 1 + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * BPW + bslot;
+    const int64_t gb = 1 + lwg * BPW + bslot;
     uint32_t* ws = reinterpret_cast<uint32_t*>(smem) + warp * up.words_per_warp;
     uint32_t* W0 = ws + lane;                                   // bitset word x at W0[x * 32]
     uint32_t* W1 = ws + up.nw * 32 + lane;                      // summary words (when !SMALL)
@@ -478,7 +512,7 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
 
 template <bool PACKED>
 __global__ void __launch_bounds__(kPipeThreads)
-chain_kernel(PipeParams p, ChainPlan cp)
+chain_kernel(SegTable tab, ChainPlan cp)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -489,8 +523,10 @@ chain_kernel(PipeParams p, ChainPlan cp)
         if (w < warp) pair_off += l; else NL = l;
     }
     if (lane >= NL) return;
-    const int64_t q = (int64_t)blockIdx.x * cp.pairs_per_cta + pair_off + lane;
-    if (q >= p.npairs) return;                          // pair j = q + 1
+    const int64_t item = (int64_t)blockIdx.x * cp.pairs_per_cta + pair_off + lane;
+    if (item >= cp.items) return;
+    int64_t q;                                          // pair j = q + 1 of its signal
+    const PipeParams p = find_signal(tab, kItemChain, item, &q);
     uint32_t* wsl = reinterpret_cast<uint32_t*>(smem) + (uint32_t)pair_off * cp.lane_words;
     chain_body<PACKED>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL);
 }
@@ -500,12 +536,14 @@ chain_kernel(PipeParams p, ChainPlan cp)
 // j, read from a shared-memory copy of the CTA's input span; y[0] = X_0[P_0[h]].
 // ===========================================================================
 __global__ void __launch_bounds__(kPipeThreads)
-epilogue_kernel(PipeParams p, int G)
+epilogue_kernel(SegTable tab, int G)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* xs = reinterpret_cast<uint32_t*>(smem);
+    int64_t cta;
+    const PipeParams p = find_signal(tab, kItemEpilogue, blockIdx.x, &cta);
     const int k = p.k;
-    const int64_t j0 = 1 + (int64_t)blockIdx.x * G;
+    const int64_t j0 = 1 + cta * G;
     const int64_t left = p.npairs - (j0 - 1);
     const int npair = (int)(left < G ? (left > 0 ? left : 0) : G);
     const int64_t ebase = (j0 - 1) * (int64_t)k;
@@ -611,17 +649,51 @@ int pipeline_max_k()
     return lo;
 }
 
-size_t pipeline_workspace_bytes(int64_t n, int k)
+// scratch of one signal: perm, rank, sorted-order links, unwind links per
+// block; joint ranks of A and B and printed nodes per pair
+static uint64_t signal_scratch_bytes(int64_t n, int k)
 {
     const int64_t nblocks = (n + k - 1) / k;
     const int64_t npairs = nblocks - 1;
     const uint64_t kp = (uint64_t)((k + 7) & ~7);
-    uint64_t b = 0;
-    b += al256(2ull * nblocks * kp);     // perm
-    b += al256(2ull * nblocks * kp);     // rnk
-    b += al256(4ull * nblocks * kp);     // slink
-    b += al256(4ull * nblocks * kp);     // ulink
-    b += al256(2ull * (npairs > 0 ? npairs : 1) * kp) * 3;   // ja, jb, out
+    const uint64_t np1 = (uint64_t)(npairs > 0 ? npairs : 1);
+    return al256(2ull * nblocks * kp) * 2 + al256(4ull * nblocks * kp) * 2 + al256(2ull * np1 * kp) * 3;
+}
+
+static void carve_signal(PipeParams& p, char*& w)
+{
+    const uint64_t kp = (uint64_t)p.kp;
+    const uint64_t np1 = (uint64_t)(p.npairs > 0 ? p.npairs : 1);
+    p.perm = (uint16_t*)w;  w += al256(2ull * p.nblocks * kp);
+    p.rnk = (uint16_t*)w;   w += al256(2ull * p.nblocks * kp);
+    p.slink = (uint32_t*)w; w += al256(4ull * p.nblocks * kp);
+    p.ulink = (uint32_t*)w; w += al256(4ull * p.nblocks * kp);
+    p.ja = (uint16_t*)w;    w += al256(2ull * np1 * kp);
+    p.jb = (uint16_t*)w;    w += al256(2ull * np1 * kp);
+    p.out = (uint16_t*)w;   w += al256(2ull * np1 * kp);
+}
+
+static void fill_signal(PipeParams& p, const uint32_t* x, uint32_t* y, int32_t* argmed,
+                        int64_t n, int k, bool is_float)
+{
+    p = PipeParams{};
+    p.x = x; p.y = y; p.argmed = argmed;
+    p.n = n; p.k = k; p.h = (k - 1) / 2;
+    p.nblocks = (n + k - 1) / k;
+    p.npairs = p.nblocks - 1;
+    p.kp = (k + 7) & ~7;
+    p.is_float = is_float;
+}
+
+size_t pipeline_workspace_bytes(int64_t n, int k)
+{
+    return (size_t)signal_scratch_bytes(n, k);
+}
+
+size_t pipeline_batched_workspace_bytes(const int64_t* n, const int32_t* k, int nseg)
+{
+    uint64_t b = al256((uint64_t)nseg * sizeof(PipeParams));
+    for (int s = 0; s < nseg; ++s) b += signal_scratch_bytes(n[s], k[s]);
     return (size_t)b;
 }
 
@@ -636,114 +708,219 @@ cudaError_t pipeline_setup()
     return cudaFuncSetAttribute(epilogue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
 }
 
-cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, bool is_float,
-                            uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes,
-                            int num_sms, cudaStream_t stream, LaunchStats* stats)
+// ---------------------------------------------------------------------------
+// Plans of one launch class (all signals with k <= kmax share the shared-
+// memory layouts sized for kmax).
+// ---------------------------------------------------------------------------
+struct ClassPlan {
+    int kmax;
+    SortPlan sp;  size_t sbytes;
+    UnwindPlan up; size_t ubytes; int uwarps; int bpw;
+    ChainPlan cp; size_t cbytes;
+    int GE;       size_t ebytes;
+};
+
+static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tuning* tune,
+                            ClassPlan* c)
 {
-    // optional timing: events before each kernel and after the last one, in
-    // the next slot of the handle's ring
+    const int W = kPipeThreads / 32;
+    c->kmax = kmax;
+    // sortmerge: the largest G that keeps two CTAs per SM (one CTA if even G = 1
+    // does not), fewer when there are few pairs to spread over the SMs
+    int G = 0;
+    for (int g = 1; g <= 64; ++g) {
+        SortPlan t;
+        size_t b;
+        if (!sort_plan(kmax, g, &t, &b)) break;
+        if (b <= (size_t)kMaxSmemBytes / 2 || g == 1) G = g;
+    }
+    if (G == 0) return false;
+    if (tune) tune += tune_class_of(kmax);
+    if (tune && tune->sort_G > 0 && tune->sort_G < G) G = tune->sort_G;
+    const int64_t want = (total_pairs + 2ll * num_sms - 1) / (2ll * num_sms);
+    if (want >= 1 && want < G) G = (int)want;
+    sort_plan(kmax, G, &c->sp, &c->sbytes);
+    c->sp.G = G;
+    // unwind
+    UnwindPlan& up = c->up;
+    up.nw = (kmax + 31) / 32;
+    up.ns = up.nw <= 32 ? 0 : (up.nw + 31) / 32;
+    up.segs = kmax >= 256 ? 4 : (kmax >= 64 ? 2 : 1);
+    up.seglen = (((kmax + up.segs - 1) / up.segs) + 7) & ~7;
+    c->bpw = 32 / up.segs;
+    const int kpmax = (kmax + 7) & ~7;
+    up.words_per_warp = (uint32_t)((up.nw + up.ns) * 32) + (uint32_t)(kpmax / 2) * (uint32_t)c->bpw;
+    int uw = W;
+    while (uw > 1 && (size_t)up.words_per_warp * 4 * uw > (size_t)kMaxSmemBytes / 2) --uw;
+    c->uwarps = uw;
+    c->ubytes = (size_t)up.words_per_warp * 4 * uw;
+    if (c->ubytes > (size_t)kMaxSmemBytes) return false;
+    // chain
+    if (!chain_plan(kmax, &c->cp, &c->cbytes)) return false;
+    // epilogue
+    c->GE = max(1, min(16, 8192 / kmax));
+    if (tune && tune->epi_G > 0) c->GE = min(c->GE, tune->epi_G);
+    c->ebytes = 4ull * (size_t)(c->GE + 1) * kmax;
+    return true;
+}
+
+static void count_items(PipeParams& p, const ClassPlan& c, int64_t* tot)
+{
+    const int64_t np = p.npairs;
+    const int64_t cnt[4] = {np > 0 ? (np + c.sp.G - 1) / c.sp.G : 1,
+                            np > 0 ? (np + c.bpw - 1) / c.bpw : 0,
+                            np,
+                            np > 0 ? (np + c.GE - 1) / c.GE : 1};
+    for (int i = 0; i < 4; ++i) { p.start[i] = tot[i]; tot[i] += cnt[i]; }
+}
+
+// Enqueue the four kernels of a set of classes: all sortmerges, then all
+// unwinds, chains and epilogues (each signal's kernels stay in order).
+static cudaError_t launch_classes(const ClassPlan* cls, const SegTable* tabs, const int64_t (*tot)[4],
+                                  int ncls, cudaStream_t stream, LaunchStats* stats)
+{
     cudaEvent_t* evs = nullptr;
     if (stats && stats->timing) {
         evs = stats->ev[stats->ring_pos % LaunchStats::kRing];
         stats->ring_pos += 1;
     }
 #define TIMER_MARK(idx) do { if (evs) cudaEventRecord(evs[idx], stream); } while (0)
-    if (ws_bytes < pipeline_workspace_bytes(n, k)) return cudaErrorInvalidValue;
-    PipeParams p{};
-    p.x = x; p.y = y; p.argmed = argmed;
-    p.n = n; p.k = k; p.h = (k - 1) / 2;
-    p.nblocks = (n + k - 1) / k;
-    p.npairs = p.nblocks - 1;
-    p.kp = (k + 7) & ~7;
-    p.is_float = is_float;
-    const uint64_t kp = (uint64_t)p.kp;
-    char* w = (char*)ws;
-    p.perm = (uint16_t*)w;  w += al256(2ull * p.nblocks * kp);
-    p.rnk = (uint16_t*)w;   w += al256(2ull * p.nblocks * kp);
-    p.slink = (uint32_t*)w; w += al256(4ull * p.nblocks * kp);
-    p.ulink = (uint32_t*)w; w += al256(4ull * p.nblocks * kp);
-    const uint64_t np1 = (uint64_t)(p.npairs > 0 ? p.npairs : 1);
-    p.ja = (uint16_t*)w;    w += al256(2ull * np1 * kp);
-    p.jb = (uint16_t*)w;    w += al256(2ull * np1 * kp);
-    p.out = (uint16_t*)w;
-
-    // ---- sortmerge: largest G that fits two CTAs per SM, else one ----------
-    SortPlan sp{};
-    size_t sbytes = 0;
-    int G = 0;
-    for (int g = 1; g <= 64; ++g) {
-        SortPlan t;
-        size_t b;
-        if (!sort_plan(k, g, &t, &b)) break;
-        if (b <= (size_t)kMaxSmemBytes / 2 || g == 1) G = g;
-    }
-    if (G == 0) return cudaErrorInvalidValue;
-    const int64_t want = (p.npairs + 2ll * num_sms - 1) / (2ll * num_sms);
-    if (want >= 1 && want < G) G = (int)want;
-    sort_plan(k, G, &sp, &sbytes);
-    sp.G = G;
-    const int W = kPipeThreads / 32;
-    int bpg = (G + 1 + W - 1) / W;
-    int cap = max(1, 2048 / k);
-    if (cap > 255) cap = 255;
-    sp.bpg = max(1, min(bpg, cap));
-    const int64_t sgrid = p.npairs > 0 ? (p.npairs + G - 1) / G : 1;
+    cudaError_t e;
     TIMER_MARK(0);
-    sortmerge_kernel<<<(unsigned)sgrid, kPipeThreads, sbytes, stream>>>(p, sp);
-    if (stats) stats->launches += 1;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-
-    if (p.npairs > 0) {
-        // ---- unwind: lanes = (block, run) pairs --------------------------------
-        UnwindPlan up{};
-        up.nw = (k + 31) / 32;
-        up.ns = up.nw <= 32 ? 0 : (up.nw + 31) / 32;
-        up.segs = k >= 256 ? 4 : (k >= 64 ? 2 : 1);
-        up.seglen = (((k + up.segs - 1) / up.segs) + 7) & ~7;
-        const int bpw = 32 / up.segs;
-        up.words_per_warp = (uint32_t)((up.nw + up.ns) * 32) + (uint32_t)(p.kp / 2) * (uint32_t)bpw;
-        int uw = W;
-        while (uw > 1 && (size_t)up.words_per_warp * 4 * uw > (size_t)kMaxSmemBytes / 2) --uw;
-        const size_t ubytes = (size_t)up.words_per_warp * 4 * uw;
-        if (ubytes > (size_t)kMaxSmemBytes) return cudaErrorInvalidValue;
-        const int64_t per_ucta = (int64_t)uw * bpw;
-        const int64_t ugrid = (p.nblocks - 1 + per_ucta - 1) / per_ucta;
-        TIMER_MARK(1);
-        if (up.ns == 0)
-            unwind_kernel<true><<<(unsigned)ugrid, 32 * uw, ubytes, stream>>>(p, up);
-        else
-            unwind_kernel<false><<<(unsigned)ugrid, 32 * uw, ubytes, stream>>>(p, up);
+    for (int c = 0; c < ncls; ++c) {
+        sortmerge_kernel<<<(unsigned)tot[c][kItemSort], kPipeThreads, cls[c].sbytes, stream>>>(tabs[c], cls[c].sp);
         if (stats) stats->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-
-        // ---- chain ----------------------------------------------------------
-        ChainPlan cp{};
-        size_t cbytes = 0;
-        if (!chain_plan(k, &cp, &cbytes)) return cudaErrorInvalidValue;
-        const int64_t cgrid = (p.npairs + cp.pairs_per_cta - 1) / cp.pairs_per_cta;
-        TIMER_MARK(2);
-        if (cp.packed)
-            chain_kernel<true><<<(unsigned)cgrid, 32 * cp.nwarps, cbytes, stream>>>(p, cp);
-        else
-            chain_kernel<false><<<(unsigned)cgrid, 32 * cp.nwarps, cbytes, stream>>>(p, cp);
-        if (stats) stats->launches += 1;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    } else {
-        TIMER_MARK(1);
-        TIMER_MARK(2);
     }
-
-    // ---- epilogue -----------------------------------------------------------
-    int GE = max(1, min(16, 8192 / k));
-    const size_t ebytes = 4ull * (size_t)(GE + 1) * k;
-    const int64_t egrid = p.npairs > 0 ? (p.npairs + GE - 1) / GE : 1;
+    TIMER_MARK(1);
+    for (int c = 0; c < ncls; ++c) {
+        if (tot[c][kItemUnwind] == 0) continue;
+        UnwindPlan up = cls[c].up;
+        up.items = tot[c][kItemUnwind];
+        const int64_t grid = (up.items + cls[c].uwarps - 1) / cls[c].uwarps;
+        if (up.ns == 0)
+            unwind_kernel<true><<<(unsigned)grid, 32 * cls[c].uwarps, cls[c].ubytes, stream>>>(tabs[c], up);
+        else
+            unwind_kernel<false><<<(unsigned)grid, 32 * cls[c].uwarps, cls[c].ubytes, stream>>>(tabs[c], up);
+        if (stats) stats->launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    TIMER_MARK(2);
+    for (int c = 0; c < ncls; ++c) {
+        if (tot[c][kItemChain] == 0) continue;
+        ChainPlan cp = cls[c].cp;
+        cp.items = tot[c][kItemChain];
+        const int64_t grid = (cp.items + cp.pairs_per_cta - 1) / cp.pairs_per_cta;
+        if (cp.packed)
+            chain_kernel<true><<<(unsigned)grid, 32 * cp.nwarps, cls[c].cbytes, stream>>>(tabs[c], cp);
+        else
+            chain_kernel<false><<<(unsigned)grid, 32 * cp.nwarps, cls[c].cbytes, stream>>>(tabs[c], cp);
+        if (stats) stats->launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     TIMER_MARK(3);
-    epilogue_kernel<<<(unsigned)egrid, kPipeThreads, ebytes, stream>>>(p, GE);
-    if (stats) stats->launches += 1;
+    for (int c = 0; c < ncls; ++c) {
+        epilogue_kernel<<<(unsigned)tot[c][kItemEpilogue], kPipeThreads, cls[c].ebytes, stream>>>(tabs[c], cls[c].GE);
+        if (stats) stats->launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     TIMER_MARK(4);
 #undef TIMER_MARK
-    return cudaGetLastError();
+    return cudaSuccess;
+}
+
+cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, bool is_float,
+                            uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes,
+                            int num_sms, cudaStream_t stream, LaunchStats* stats)
+{
+    if (ws_bytes < pipeline_workspace_bytes(n, k)) return cudaErrorInvalidValue;
+    SegTable tab{};
+    tab.segs = nullptr;
+    tab.nseg = 1;
+    fill_signal(tab.one, x, y, argmed, n, k, is_float);
+    char* w = (char*)ws;
+    carve_signal(tab.one, w);
+    ClassPlan cls;
+    if (!make_class_plan(k, tab.one.npairs, num_sms, stats ? stats->tune : nullptr, &cls))
+        return cudaErrorInvalidValue;
+    int64_t tot[1][4] = {{0, 0, 0, 0}};
+    count_items(tab.one, cls, tot[0]);
+    return launch_classes(&cls, &tab, tot, 1, stream, stats);
+}
+
+// Class boundaries: the packed list format ends at k = 1021, the one-word
+// unwind summary at k = 1024; smaller classes keep the shared-memory layouts
+// of small k.
+static const int kClassMax[] = {64, 256, 1021, 2047, 4095, 1 << 30};
+constexpr int kNumClasses = kNumTuneClasses;
+
+int tune_class_of(int k)
+{
+    int c = 0;
+    while (k > kClassMax[c]) ++c;
+    return c;
+}
+
+cudaError_t launch_pipeline_batched(const uint32_t* x, uint32_t* y, int32_t* argmed, bool is_float,
+                                    const int64_t* x_off, const int64_t* n, const int64_t* y_off,
+                                    const int32_t* k, int nseg, void* ws, size_t ws_bytes,
+                                    void* stage, size_t stage_bytes, int num_sms,
+                                    cudaStream_t stream, LaunchStats* stats)
+{
+    if (nseg <= 0) return cudaSuccess;
+    if (ws_bytes < pipeline_batched_workspace_bytes(n, k, nseg)) return cudaErrorInvalidValue;
+    if (stage_bytes < (size_t)nseg * sizeof(PipeParams)) return cudaErrorInvalidValue;
+    // signals grouped by class, descriptors written class by class
+    int cls_of_first[kNumClasses + 1];
+    int count[kNumClasses] = {0};
+    int kmax[kNumClasses] = {0};
+    int64_t pairs[kNumClasses] = {0};
+    auto class_of = [&](int kk) { int c = 0; while (kk > kClassMax[c]) ++c; return c; };
+    for (int s = 0; s < nseg; ++s) {
+        const int c = class_of(k[s]);
+        count[c] += 1;
+        kmax[c] = max(kmax[c], k[s]);
+        pairs[c] += (n[s] + k[s] - 1) / k[s] - 1;
+    }
+    cls_of_first[0] = 0;
+    for (int c = 0; c < kNumClasses; ++c) cls_of_first[c + 1] = cls_of_first[c] + count[c];
+    ClassPlan plans[kNumClasses];
+    SegTable tabs[kNumClasses];
+    int64_t tot[kNumClasses][4];
+    int ncls = 0;
+    int cls_index[kNumClasses];
+    for (int c = 0; c < kNumClasses; ++c) {
+        if (!count[c]) continue;
+        if (!make_class_plan(kmax[c], pairs[c], num_sms, stats ? stats->tune : nullptr, &plans[ncls]))
+            return cudaErrorInvalidValue;
+        cls_index[c] = ncls;
+        for (int i = 0; i < 4; ++i) tot[ncls][i] = 0;
+        ++ncls;
+    }
+    PipeParams* host = (PipeParams*)stage;
+    PipeParams* dev = (PipeParams*)ws;
+    char* w = (char*)ws + al256((uint64_t)nseg * sizeof(PipeParams));
+    int fillpos[kNumClasses];
+    for (int c = 0; c < kNumClasses; ++c) fillpos[c] = cls_of_first[c];
+    for (int s = 0; s < nseg; ++s) {
+        const int c = class_of(k[s]);
+        PipeParams& p = host[fillpos[c]++];
+        fill_signal(p, x + x_off[s], y + y_off[s], argmed ? argmed + y_off[s] : nullptr,
+                    n[s], k[s], is_float);
+        carve_signal(p, w);
+        count_items(p, plans[cls_index[c]], tot[cls_index[c]]);
+    }
+    for (int c = 0; c < kNumClasses; ++c) {
+        if (!count[c]) continue;
+        SegTable& t = tabs[cls_index[c]];
+        t.segs = dev + cls_of_first[c];
+        t.nseg = count[c];
+        t.one = PipeParams{};
+    }
+    cudaError_t e = cudaMemcpyAsync(dev, host, (size_t)nseg * sizeof(PipeParams),
+                                    cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return e;
+    return launch_classes(plans, tabs, tot, ncls, stream, stats);
 }
 
 }  // namespace mf
