@@ -318,6 +318,9 @@ def run_ours(args):
     e2e_s = reduce_max(dist, time.perf_counter() - t0, dev)
     e2e_value = ws * m * e2e_steps / e2e_s / 1e9
 
+    batched = None if args.skip_extra else bench_batched(mf, h, dev, stream, seed, args)
+    gradient = None if args.skip_extra else bench_gradient(dev, stream, seed, args)
+
     peak, peak_kind = peaks()
     alg_bytes = 4 * N_SIG + 4 * m
     dom = max(kt, key=kt.get)                     # dominant kernel, CUDA-event average
@@ -352,6 +355,8 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "step_frac": alg_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
         "kernels_ms": kt,
+        "batched": batched,
+        "gradient": gradient,
         "clocks": clocks,
         "gpu_launches": launches,
         "cpu_baseline": cpu,
@@ -364,6 +369,88 @@ def run_ours(args):
     return 0
 
 
+def bench_batched(mf, h, dev, stream, seed, args):
+    """4096 signals of log-uniform n and k in one batched call (captured in a
+    CUDA graph and replayed) against a loop of per-signal calls."""
+    import torch
+    from signals import batched_signals
+    b = batched_signals(nseg=4096, seed=seed)
+    x = torch.from_numpy(b.x).to(dev)
+    y = torch.empty(b.y_total, dtype=torch.float32, device=dev)
+    segs = mf.make_segments(b.n, b.k, b.x_off, b.y_off)
+    with torch.cuda.stream(stream):
+        mf.mf_filter_batched(h, x, y, segs)
+    stream.synchronize()
+    l0 = mf.mf_launch_count(h)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        mf.mf_set_stream(h, torch.cuda.current_stream(dev))
+        mf.mf_filter_batched(h, x, y, segs)
+    launches_per_call = mf.mf_launch_count(h) - l0
+    mf.mf_set_stream(h, stream)
+    reps = max(3, min(args.steps, 10))
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            g.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e1.record(stream)
+    stream.synchronize()
+    graph_ms = e0.elapsed_time(e1) / reps
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            mf.mf_filter_batched(h, x, y, segs)
+        e1.record(stream)
+    stream.synchronize()
+    batched_ms = e0.elapsed_time(e1) / reps
+    ys = [torch.empty(int(b.n[s] - b.k[s] + 1), device=dev) for s in range(len(b.n))]
+    xs = [x[int(b.x_off[s]):int(b.x_off[s] + b.n[s])] for s in range(len(b.n))]
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for s in range(len(b.n)):
+            mf.mf_filter(h, xs[s], int(b.k[s]), ys[s])
+        e1.record(stream)
+    stream.synchronize()
+    loop_ms = e0.elapsed_time(e1)
+    return {"workload": "4096 float32 signals, n log-uniform [1e3, 262144], odd k log-uniform "
+                        "[3, 4095], 10% +-1e3 impulses",
+            "outputs": int(b.y_total), "graph_ms": graph_ms, "batched_ms": batched_ms,
+            "per_signal_loop_ms": loop_ms, "launches_per_batched_call": int(launches_per_call),
+            "value_graph": b.y_total / (graph_ms * 1e-3) / 1e9,
+            "value_per_signal": b.y_total / (loop_ms * 1e-3) / 1e9, "unit": UNIT,
+            "speedup_vs_per_signal": loop_ms / graph_ms}
+
+
+def bench_gradient(dev, stream, seed, args):
+    """Forward (with argmedian) and backward of 64 float32 signals, n = 65536,
+    k = 63, distinct values, upstream gradient N(0, 1)."""
+    import torch
+    from paper_1406_1717_gb300.autograd import median_filter
+    from signals import distinct_f32
+    rows, n, k = 64, 65536, 63
+    x = torch.from_numpy(np.stack([distinct_f32(n, seed=seed + r) for r in range(rows)])).to(dev)
+    gy = torch.from_numpy(np.random.default_rng(seed).standard_normal((rows, n - k + 1))
+                          .astype(np.float32)).to(dev)
+    reps = max(3, min(args.steps, 10))
+    with torch.cuda.stream(stream):
+        for it in range(reps + 2):
+            if it == 2:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            xr = x.detach().requires_grad_(True)
+            y = median_filter(xr, k)
+            y.backward(gy)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": "64 x 65536 float32, k=63, forward + backward", "fwd_bwd_ms": ms,
+            "value": rows * (n - k + 1) / (ms * 1e-3) / 1e9, "unit": UNIT}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,6 +460,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-windows", type=int, default=100_000)
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="skip the batched and gradient configurations")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

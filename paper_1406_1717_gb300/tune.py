@@ -1,0 +1,87 @@
+"""Autotuner of the launch plans, per window-size class.
+
+For each class of k (<= 64, <= 256, <= 1021, <= 2047, <= 4095) the tuner
+times the candidate numbers of block pairs per CTA of the sort+merge kernel
+and of the store kernel on a seeded random-walk signal, with the library's
+CUDA-event kernel timing (mf_set_timing / mf_kernel_times), and applies the
+fastest choice with mf_set_tuning.  Results are cached as JSON (path from
+MF_TUNE_CACHE, default paper_1406_1717_gb300/_tune_cache.json) and can be
+reloaded onto any handle of the same GPU model.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from . import (mf_filter, mf_kernel_times, mf_set_stream, mf_set_timing, mf_set_tuning,
+               mf_sync)
+
+CLASS_K = (63, 255, 1001, 2047, 4095)          # one representative k per class
+SORT_CANDIDATES = (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64)
+STORE_CANDIDATES = (1, 2, 4, 8, 16)
+_PKG = os.path.dirname(os.path.abspath(__file__))
+
+
+def cache_path() -> str:
+    return os.environ.get("MF_TUNE_CACHE", os.path.join(_PKG, "_tune_cache.json"))
+
+
+def _time_kernel(h, x, k, which, reps=5):
+    y = torch.empty(x.numel() - k + 1, dtype=x.dtype, device=x.device)
+    mf_filter(h, x, k, y)                        # warm-up (and workspace)
+    mf_set_timing(h, True)
+    for _ in range(reps):
+        mf_filter(h, x, k, y)
+    mf_sync(h)
+    t = mf_kernel_times(h, reps)[which] / reps
+    mf_set_timing(h, False)
+    return t
+
+
+def autotune(h, device=0, n=1 << 22, seed=20140607, classes=CLASS_K) -> dict:
+    """Tune every class on handle h; returns {k: {...}} and applies it."""
+    from signals import random_walk_f32
+    dev = torch.device("cuda", device)
+    mf_set_stream(h, torch.cuda.current_stream(dev))
+    x = torch.from_numpy(random_walk_f32(n, seed=seed)).to(dev)
+    result = {}
+    for k in classes:
+        best_g, best_t = 0, float("inf")
+        for g in SORT_CANDIDATES:
+            mf_set_tuning(h, k, g, 0)
+            t = _time_kernel(h, x, k, "sortmerge")
+            if t < best_t:
+                best_g, best_t = g, t
+        best_e, best_te = 0, float("inf")
+        for e in STORE_CANDIDATES:
+            mf_set_tuning(h, k, best_g, e)
+            t = _time_kernel(h, x, k, "epilogue")
+            if t < best_te:
+                best_e, best_te = e, t
+        mf_set_tuning(h, k, best_g, best_e)
+        result[str(k)] = {"sort_pairs_per_cta": best_g, "store_pairs_per_cta": best_e,
+                          "sortmerge_ms": best_t, "epilogue_ms": best_te}
+    return result
+
+
+def save(result: dict, path: str = None) -> str:
+    path = path or cache_path()
+    meta = {"gpu": torch.cuda.get_device_name(0) if torch.cuda.is_available() else None,
+            "classes": result}
+    with open(path, "w") as f:
+        json.dump(meta, f, indent=1)
+    return path
+
+
+def load(h, path: str = None) -> bool:
+    """Apply a cached tuning to handle h; False if there is no cache."""
+    path = path or cache_path()
+    if not os.path.exists(path):
+        return False
+    with open(path) as f:
+        meta = json.load(f)
+    for k, v in meta.get("classes", {}).items():
+        mf_set_tuning(h, int(k), int(v["sort_pairs_per_cta"]), int(v["store_pairs_per_cta"]))
+    return True

@@ -1,0 +1,57 @@
+"""Autotuner: tunes a class, applies and persists the choice; results stay
+bit-exact under every tuned plan."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1406_1717_gb300 as mf
+from paper_1406_1717_gb300 import tune
+from signals import random_walk_f32
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def test_autotune_one_class_and_reload(tmp_path):
+    h = mf.mf_create(0, torch.cuda.current_stream(DEV))
+    try:
+        res = tune.autotune(h, n=1 << 18, classes=(255,))
+        assert set(res) == {"255"}
+        g = res["255"]["sort_pairs_per_cta"]
+        assert g in tune.SORT_CANDIDATES
+        path = tune.save(res, str(tmp_path / "tune.json"))
+        assert json.load(open(path))["classes"]["255"]["sort_pairs_per_cta"] == g
+        h2 = mf.mf_create(0, torch.cuda.current_stream(DEV))
+        try:
+            assert tune.load(h2, path)
+            x_np = random_walk_f32(50_003, seed=4)
+            x = torch.from_numpy(x_np).to(DEV)
+            for k in (201, 255):
+                y = torch.empty(x_np.size - k + 1, device=DEV)
+                mf.mf_filter(h2, x, k, y)
+                mf.mf_sync(h2)
+                ry, _ = oracle.median_filter(x_np, k)
+                np.testing.assert_array_equal(y.cpu().numpy().view(np.uint32), ry.view(np.uint32))
+        finally:
+            mf.mf_destroy(h2)
+    finally:
+        mf.mf_destroy(h)
+
+
+@pytest.mark.parametrize("g", [1, 2, 5, 13])
+def test_every_sort_plan_is_exact(g):
+    h = mf.mf_create(0, torch.cuda.current_stream(DEV))
+    try:
+        mf.mf_set_tuning(h, 1001, g, 3)
+        x_np = random_walk_f32(60_011, seed=g)
+        x = torch.from_numpy(x_np).to(DEV)
+        y = torch.empty(x_np.size - 1001 + 1, device=DEV)
+        mf.mf_filter(h, x, 1001, y)
+        mf.mf_sync(h)
+        ry, _ = oracle.median_filter(x_np, 1001)
+        np.testing.assert_array_equal(y.cpu().numpy().view(np.uint32), ry.view(np.uint32))
+    finally:
+        mf.mf_destroy(h)
