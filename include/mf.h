@@ -91,8 +91,13 @@ mf_status mf_set_stream(mf_handle h, void* cuda_stream);
 /* Median filter of one signal (paper Section 1; method Sections 3-5).
  *  x       device pointer, n elements of `dtype` (input, not modified)
  *  n       signal length, n >= k
- *  k       odd window size, 1 <= k <= n (k <= 8004 in this build: one
- *          block pair must fit in shared memory)
+ *  k       odd window size, 1 <= k <= n and k <= 1,048,575.  Up to about
+ *          8004 (one block pair in shared memory) the shared-memory pipeline
+ *          runs; above it the large-k tier: global-memory merge tiers for the
+ *          block sort and the post-processing chain of each block pair split
+ *          into up to 32 segments, each started from a state rebuilt with the
+ *          invariant of Section 5.3 (workspace about 44 + 12 * segments bytes
+ *          per sample)
  *  y       device pointer, n-k+1 elements of `dtype` (output, overwritten)
  *  argmed  device pointer to n-k+1 int32 (output) or NULL; needs n <= 2^31-1
  * y and argmed must not overlap x.
@@ -118,7 +123,9 @@ mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_
  * Output ranges must not overlap each other or x.
  * The signals are grouped by window size into at most six classes and each
  * class runs as one launch per kernel (at most 24 launches per call,
- * whatever nseg is).  The call can be captured into a CUDA graph: make one
+ * whatever nseg is).  Signals whose k is above the shared-memory pipeline's
+ * limit follow, one large-k launch sequence each (7 + log2(k / 1024)
+ * launches), in the same workspace.  The call can be captured into a CUDA graph: make one
  * uncaptured call with the same sizes first (it allocates the workspace and
  * a pinned descriptor buffer; during capture nothing may be allocated and
  * such calls return MF_ERR_OOM).  A captured call's descriptors stay with

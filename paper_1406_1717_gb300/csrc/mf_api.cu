@@ -86,6 +86,21 @@ mf_status ensure_workspace(mf_handle h, size_t bytes) {
 
 mf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MF_OK : MF_ERR_CUDA; }
 
+// Workspace of one signal: shared-memory pipeline up to pipeline_max_k(),
+// the global-memory large-k tier above it.
+size_t signal_workspace_bytes(int64_t n, int k) {
+    return k <= mf::pipeline_max_k() ? mf::pipeline_workspace_bytes(n, k)
+                                     : mf::large_workspace_bytes(n, k);
+}
+
+cudaError_t launch_signal(mf_handle h, const uint32_t* x, int64_t n, int k, bool is_float,
+                          uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes) {
+    if (k <= mf::pipeline_max_k())
+        return mf::launch_pipeline(x, n, k, is_float, y, argmed, ws, ws_bytes, h->num_sms,
+                                   h->stream, &h->stats);
+    return mf::launch_large(x, n, k, is_float, y, argmed, ws, ws_bytes, h->stream, &h->stats);
+}
+
 }  // namespace
 
 extern "C" {
@@ -101,7 +116,9 @@ mf_status mf_create(mf_handle* out, int device, void* cuda_stream, size_t max_wo
     if (prop.major != 10 || prop.minor != 3) return MF_ERR_DEVICE;
     DeviceGuard g(device);
     if (!g.ok) return MF_ERR_CUDA;
-    if (mf::pipeline_setup() != cudaSuccess || mf::backward_setup() != cudaSuccess) return MF_ERR_CUDA;
+    if (mf::pipeline_setup() != cudaSuccess || mf::large_setup() != cudaSuccess ||
+        mf::backward_setup() != cudaSuccess)
+        return MF_ERR_CUDA;
     mf_ctx* h = new (std::nothrow) mf_ctx();
     if (!h) return MF_ERR_OOM;
     h->device = device;
@@ -110,7 +127,7 @@ mf_status mf_create(mf_handle* out, int device, void* cuda_stream, size_t max_wo
     h->ws = nullptr;
     h->ws_size = 0;
     h->num_sms = prop.multiProcessorCount;
-    h->max_k = mf::pipeline_max_k();
+    h->max_k = mf::kLargeMaxK;
     h->events_made = false;
     for (int c = 0; c < mf::kNumTuneClasses; ++c) h->tune[c] = mf::Tuning{0, 0};
     h->stats.tune = h->tune;
@@ -143,12 +160,11 @@ mf_status mf_filter(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32
         return MF_ERR_OVERLAP;
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
-    const size_t need = mf::pipeline_workspace_bytes(n, k);
+    const size_t need = signal_workspace_bytes(n, k);
     st = ensure_workspace(h, need);
     if (st != MF_OK) return st;
-    return cuda_status(mf::launch_pipeline((const uint32_t*)x, n, k, dtype == MF_FLOAT32,
-                                           (uint32_t*)y, argmed, h->ws, need, h->num_sms,
-                                           h->stream, &h->stats));
+    return cuda_status(launch_signal(h, (const uint32_t*)x, n, k, dtype == MF_FLOAT32,
+                                     (uint32_t*)y, argmed, h->ws, need));
 }
 
 mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_t n, int32_t k,
@@ -163,7 +179,7 @@ mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
     const size_t io = xb + yb + (argmed_host ? yb : 0);
-    const size_t need = mf::pipeline_workspace_bytes(n, k);
+    const size_t need = signal_workspace_bytes(n, k);
     st = ensure_workspace(h, io + need);
     if (st != MF_OK) return st;
     char* base = (char*)h->ws;
@@ -172,8 +188,7 @@ mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_
     int32_t* ad = argmed_host ? (int32_t*)(base + xb + yb) : nullptr;
     cudaError_t e = cudaMemcpyAsync(xd, x_host, 4 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = mf::launch_pipeline(xd, n, k, dtype == MF_FLOAT32, yd, ad, base + io, need,
-                                h->num_sms, h->stream, &h->stats);
+        e = launch_signal(h, xd, n, k, dtype == MF_FLOAT32, yd, ad, base + io, need);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(y_host, yd, 4 * m, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess && ad)
@@ -211,15 +226,39 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
     if (nseg == 0) return MF_OK;
-    std::vector<int64_t> xo((size_t)nseg), nn((size_t)nseg), yo((size_t)nseg);
-    std::vector<int32_t> kk((size_t)nseg);
+    // signals of the shared-memory pipeline go into one batched launch group;
+    // the large-k ones follow one by one, reusing the same workspace
+    std::vector<int64_t> xo, nn, yo;
+    std::vector<int32_t> kk, big;
+    const int kmax_pipe = mf::pipeline_max_k();
+    size_t big_need = 0;
     for (int32_t s = 0; s < nseg; ++s) {
-        xo[s] = segs[s].x_off; nn[s] = segs[s].n; yo[s] = segs[s].y_off; kk[s] = segs[s].k;
+        if (segs[s].k > kmax_pipe) {
+            big.push_back(s);
+            big_need = std::max(big_need, mf::large_workspace_bytes(segs[s].n, segs[s].k));
+            continue;
+        }
+        xo.push_back(segs[s].x_off); nn.push_back(segs[s].n);
+        yo.push_back(segs[s].y_off); kk.push_back(segs[s].k);
     }
-    const size_t need = mf::pipeline_batched_workspace_bytes(nn.data(), kk.data(), nseg);
+    const int32_t nsmall = (int32_t)kk.size();
+    const size_t small_need =
+        nsmall ? mf::pipeline_batched_workspace_bytes(nn.data(), kk.data(), nsmall) : 0;
+    const size_t need = std::max(small_need, big_need);
     mf_status st = ensure_workspace(h, need);
     if (st != MF_OK) return st;
-    const size_t stage_need = (size_t)nseg * sizeof(mf::PipeParams);
+    const bool is_float = dtype == MF_FLOAT32;
+    if (nsmall == 0) {
+        for (int32_t s : big) {
+            const mf_segment& d = segs[s];
+            cudaError_t e = mf::launch_large((const uint32_t*)x + d.x_off, d.n, d.k, is_float,
+                                             (uint32_t*)y + d.y_off, argmed ? argmed + d.y_off : nullptr,
+                                             h->ws, need, h->stream, &h->stats);
+            if (e != cudaSuccess) return MF_ERR_CUDA;
+        }
+        return MF_OK;
+    }
+    const size_t stage_need = (size_t)nsmall * sizeof(mf::PipeParams);
     const bool cap = capturing(h->stream);
     if (!cap) {
         if (h->stage_in_graph) {                      // leave that buffer to its graph
@@ -241,10 +280,17 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
         return MF_ERR_OOM;                            // make one uncaptured call of this size first
     }
     cudaError_t e = mf::launch_pipeline_batched((const uint32_t*)x, (uint32_t*)y, argmed,
-                                                dtype == MF_FLOAT32, xo.data(), nn.data(), yo.data(),
-                                                kk.data(), nseg, h->ws, need, h->stage, h->stage_size,
+                                                is_float, xo.data(), nn.data(), yo.data(),
+                                                kk.data(), nsmall, h->ws, need, h->stage, h->stage_size,
                                                 h->num_sms, h->stream, &h->stats);
     if (e != cudaSuccess) return MF_ERR_CUDA;
+    for (int32_t s : big) {
+        const mf_segment& d = segs[s];
+        e = mf::launch_large((const uint32_t*)x + d.x_off, d.n, d.k, is_float,
+                             (uint32_t*)y + d.y_off, argmed ? argmed + d.y_off : nullptr,
+                             h->ws, need, h->stream, &h->stats);
+        if (e != cudaSuccess) return MF_ERR_CUDA;
+    }
     if (cap) h->stage_in_graph = true;
     else cudaEventRecord(h->stage_done, h->stream);
     return MF_OK;

@@ -90,6 +90,16 @@ cudaError_t launch_pipeline_batched(const uint32_t* x, uint32_t* y, int32_t* arg
                                     void* stage, size_t stage_bytes, int num_sms,
                                     cudaStream_t stream, LaunchStats* stats);
 
+// ---- large-k tier (mf_large.cu): pipeline_max_k() < k <= kLargeMaxK -------
+constexpr int kLargeMaxK = (1 << 20) - 1;
+constexpr int kLargeSegSteps = 1024;   // target steps per chain segment
+constexpr int kLargeMaxSegs = 32;      // segments per block pair at most
+size_t large_workspace_bytes(int64_t n, int k);
+cudaError_t large_setup();
+cudaError_t launch_large(const uint32_t* x, int64_t n, int k, bool is_float, uint32_t* y,
+                         int32_t* argmed, void* ws, size_t ws_bytes, cudaStream_t stream,
+                         LaunchStats* stats);
+
 cudaError_t backward_setup();
 cudaError_t launch_backward(const float* gy, const int32_t* argmed, int64_t n, int k,
                             float* gx, cudaStream_t stream, uint64_t* launches);

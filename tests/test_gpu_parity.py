@@ -158,21 +158,19 @@ def test_full_size_k1001_sampled(handle, kind):
 
 
 def test_max_supported_k_and_unsupported(handle):
+    """k up to 2^20 - 1 is served (large k by the global-memory tier); above it
+    the call is refused with MF_ERR_UNSUPPORTED before any work."""
     lib = mf.load_library()
-    kmax = None
-    for k in (16383, 8191, 6001, 5001, 4095):
-        x = uniform_f32(2 * k + 3, seed=k)
-        xd = torch.from_numpy(x).to(DEV)
-        yd = torch.empty(x.size - k + 1, device=DEV)
-        st = lib.mf_filter(handle, 1, xd.data_ptr(), x.size, k, yd.data_ptr(), None)
-        if st == 0:
-            kmax = k
-            mf.mf_sync(handle)
-            ry, _ = oracle.median_filter(x, k)
-            assert_bits_equal(yd.cpu().numpy(), ry, f"k={k}")
-            break
-        assert st == 8   # MF_ERR_UNSUPPORTED
-    assert kmax is not None and kmax >= 4095
+    k = (1 << 20) + 1
+    xd = torch.zeros(k + 2, device=DEV)
+    yd = torch.empty(3, device=DEV)
+    assert lib.mf_filter(handle, 1, xd.data_ptr(), k + 2, k, yd.data_ptr(), None) == 8
+    k = 16383
+    x = uniform_f32(2 * k + 3, seed=k)
+    y, a = gpu_filter(handle, x, k)
+    ry, ra = oracle.median_filter(x, k)
+    assert_bits_equal(y, ry, f"k={k}")
+    np.testing.assert_array_equal(a, ra)
 
 
 def test_argument_errors(handle):
