@@ -91,12 +91,13 @@ mf_status mf_set_stream(mf_handle h, void* cuda_stream);
 /* Median filter of one signal (paper Section 1; method Sections 3-5).
  *  x       device pointer, n elements of `dtype` (input, not modified)
  *  n       signal length, n >= k
- *  k       odd window size, 1 <= k <= n and k <= 1,048,575.  Up to about
- *          8004 (one block pair in shared memory) the shared-memory pipeline
- *          runs; above it the large-k tier: global-memory merge tiers for the
+ *  k       odd window size, 1 <= k <= n and k <= 262,143.  Below 5001
+ *          (the handle's tier threshold, see mf_set_tier_threshold; at most
+ *          9,344, one block pair in shared memory) the shared-memory
+ *          pipeline runs; from it the large-k tier: global-memory merge tiers for the
  *          block sort and the post-processing chain of each block pair split
  *          into up to 32 segments, each started from a state rebuilt with the
- *          invariant of Section 5.3 (workspace about 44 + 12 * segments bytes
+ *          invariant of Section 5.3 (workspace about 48 + 8 * segments bytes
  *          per sample)
  *  y       device pointer, n-k+1 elements of `dtype` (output, overwritten)
  *  argmed  device pointer to n-k+1 int32 (output) or NULL; needs n <= 2^31-1
@@ -185,6 +186,32 @@ mf_status mf_launch_count(mf_handle h, uint64_t* count);
  * Used by the autotuner in paper_1406_1717_gb300/tune.py. */
 mf_status mf_set_tuning(mf_handle h, int32_t k, int32_t sort_pairs_per_cta,
                         int32_t store_pairs_per_cta);
+
+/* Device workspace (bytes) that mf_filter_batched with these descriptors
+ * needs on this handle (host-only computation; the request server admits
+ * work by it).  Errors: MF_ERR_NULL, MF_ERR_BAD_SEGMENT. */
+mf_status mf_batched_workspace_bytes(mf_handle h, const mf_segment* segs_host, int32_t nseg,
+                                     size_t* bytes);
+
+/* Bytes of device workspace the handle currently holds. */
+mf_status mf_workspace_size(mf_handle h, size_t* bytes);
+
+/* Wait for the handle's stream and free its device workspace (the next call
+ * allocates again).  Errors: MF_ERR_NULL, MF_ERR_UNSUPPORTED (stream being
+ * captured), MF_ERR_CUDA. */
+mf_status mf_release_workspace(mf_handle h);
+
+/* Window size from which calls on this handle use the large-k tier instead
+ * of the shared-memory pipeline (k >= k_large_from; k above the pipeline's
+ * limit of 9,344 always uses it).  0 restores the built-in crossover (5001,
+ * measured on GB300); values above the pipeline's limit are capped to it.  Both tiers give the same results; the threshold only
+ * chooses the faster one (the autotuner in paper_1406_1717_gb300/tune.py
+ * measures the crossover).  Errors: MF_ERR_NULL, MF_ERR_K_GT_N (k < 0). */
+mf_status mf_set_tier_threshold(mf_handle h, int32_t k_large_from);
+
+/* The handle's current threshold: calls with k >= *k_large_from use the
+ * large-k tier. */
+mf_status mf_get_tier_threshold(mf_handle h, int32_t* k_large_from);
 
 /* Per-kernel timing for measurement.  With timing enabled, every mf_filter /
  * mf_filter_host call records CUDA events on the handle's stream around its

@@ -73,6 +73,12 @@ def load_library(path: str = LIB_PATH):
             "mf_launch_count": ([vp, c.POINTER(c.c_uint64)], c.c_int),
             "mf_set_timing": ([vp, c.c_int], c.c_int),
             "mf_set_tuning": ([vp, i32, i32, i32], c.c_int),
+            "mf_set_tier_threshold": ([vp, i32], c.c_int),
+            "mf_get_tier_threshold": ([vp, c.POINTER(i32)], c.c_int),
+            "mf_batched_workspace_bytes": ([vp, vp, i32, c.POINTER(sz)], c.c_int),
+            "mf_workspace_size": ([vp, c.POINTER(sz)], c.c_int),
+            "mf_release_workspace": ([vp], c.c_int),
+            "mf_fill_splitmix": ([c.c_int, vp, i64, c.c_uint64, vp], c.c_int),
             "mf_kernel_times": ([vp, i32, c.POINTER(c.c_float)], c.c_int),
             "mf_status_str": ([c.c_int], c.c_char_p),
             "mf_destroy": ([vp], c.c_int),
@@ -212,6 +218,54 @@ def mf_set_tuning(handle, k: int, sort_pairs_per_cta: int = 0, store_pairs_per_c
     """Launch-plan choice for the window-size class containing k (0 = built-in)."""
     _check(load_library().mf_set_tuning(handle, int(k), int(sort_pairs_per_cta),
                                         int(store_pairs_per_cta)), "mf_set_tuning")
+
+
+def mf_set_tier_threshold(handle, k_large_from: int = 0):
+    """Calls with k >= k_large_from use the large-k tier (0 = the pipeline's limit)."""
+    _check(load_library().mf_set_tier_threshold(handle, int(k_large_from)),
+           "mf_set_tier_threshold")
+
+
+def mf_get_tier_threshold(handle) -> int:
+    out = ctypes.c_int32()
+    _check(load_library().mf_get_tier_threshold(handle, ctypes.byref(out)), "mf_get_tier_threshold")
+    return int(out.value)
+
+
+def tier_of(handle, k: int) -> str:
+    """"large" if calls with window k on this handle run the large-k tier, else "pipeline"."""
+    return "large" if int(k) >= mf_get_tier_threshold(handle) else "pipeline"
+
+
+def mf_batched_workspace_bytes(handle, segs: np.ndarray) -> int:
+    """Workspace bytes mf_filter_batched needs for these descriptors on this handle."""
+    segs = np.ascontiguousarray(segs, dtype=SEGMENT_DTYPE)
+    out = ctypes.c_size_t()
+    _check(load_library().mf_batched_workspace_bytes(handle, segs.ctypes.data, len(segs),
+                                                     ctypes.byref(out)),
+           "mf_batched_workspace_bytes")
+    return int(out.value)
+
+
+def mf_workspace_size(handle) -> int:
+    out = ctypes.c_size_t()
+    _check(load_library().mf_workspace_size(handle, ctypes.byref(out)), "mf_workspace_size")
+    return int(out.value)
+
+
+def mf_release_workspace(handle):
+    _check(load_library().mf_release_workspace(handle), "mf_release_workspace")
+
+
+def mf_fill_splitmix(x, seed: int, stream=None):
+    """Fill the CUDA tensor x (int32 or float32) with SplitMix64 payload samples."""
+    import torch
+    if not x.is_cuda or not x.is_contiguous():
+        raise TypeError("x must be a contiguous CUDA tensor")
+    s = stream if stream is not None else torch.cuda.current_stream(x.device)
+    _check(load_library().mf_fill_splitmix(_dtype_code(x), x.data_ptr(), x.numel(),
+                                           int(seed) & 0xFFFFFFFFFFFFFFFF, s.cuda_stream),
+           "mf_fill_splitmix")
 
 
 def mf_set_timing(handle, enable: bool = True):

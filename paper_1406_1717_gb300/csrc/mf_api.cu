@@ -20,6 +20,8 @@ struct mf_ctx {
     size_t ws_size;
     int num_sms;
     int max_k;
+    int large_from_k;         // k >= this runs the large-k tier (k above the
+                              // shared-memory pipeline's limit always does)
     mf::LaunchStats stats;
     bool events_made;
     mf::Tuning tune[mf::kNumTuneClasses];
@@ -88,14 +90,36 @@ mf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MF_OK : MF_ERR_
 
 // Workspace of one signal: shared-memory pipeline up to pipeline_max_k(),
 // the global-memory large-k tier above it.
-size_t signal_workspace_bytes(int64_t n, int k) {
-    return k <= mf::pipeline_max_k() ? mf::pipeline_workspace_bytes(n, k)
-                                     : mf::large_workspace_bytes(n, k);
+bool use_large(mf_handle h, int k) {
+    return k >= h->large_from_k || k > mf::pipeline_max_k();
+}
+
+size_t signal_workspace_bytes(mf_handle h, int64_t n, int k) {
+    return use_large(h, k) ? mf::large_workspace_bytes(n, k) : mf::pipeline_workspace_bytes(n, k);
+}
+
+// Workspace of a batched call: the pipeline group and, reusing the same
+// memory afterwards, the largest large-k signal.
+size_t batched_need(mf_handle h, const mf_segment* segs, int32_t nseg) {
+    std::vector<int64_t> nn;
+    std::vector<int32_t> kk;
+    size_t big_need = 0;
+    for (int32_t s = 0; s < nseg; ++s) {
+        if (use_large(h, segs[s].k)) {
+            big_need = std::max(big_need, mf::large_workspace_bytes(segs[s].n, segs[s].k));
+        } else {
+            nn.push_back(segs[s].n);
+            kk.push_back(segs[s].k);
+        }
+    }
+    const size_t small_need =
+        kk.empty() ? 0 : mf::pipeline_batched_workspace_bytes(nn.data(), kk.data(), (int)kk.size());
+    return std::max(small_need, big_need);
 }
 
 cudaError_t launch_signal(mf_handle h, const uint32_t* x, int64_t n, int k, bool is_float,
                           uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes) {
-    if (k <= mf::pipeline_max_k())
+    if (!use_large(h, k))
         return mf::launch_pipeline(x, n, k, is_float, y, argmed, ws, ws_bytes, h->num_sms,
                                    h->stream, &h->stats);
     return mf::launch_large(x, n, k, is_float, y, argmed, ws, ws_bytes, h->stream, &h->stats);
@@ -128,6 +152,7 @@ mf_status mf_create(mf_handle* out, int device, void* cuda_stream, size_t max_wo
     h->ws_size = 0;
     h->num_sms = prop.multiProcessorCount;
     h->max_k = mf::kLargeMaxK;
+    h->large_from_k = std::min(mf::kLargeFromK, mf::pipeline_max_k() + 1);
     h->events_made = false;
     for (int c = 0; c < mf::kNumTuneClasses; ++c) h->tune[c] = mf::Tuning{0, 0};
     h->stats.tune = h->tune;
@@ -160,7 +185,7 @@ mf_status mf_filter(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32
         return MF_ERR_OVERLAP;
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
-    const size_t need = signal_workspace_bytes(n, k);
+    const size_t need = signal_workspace_bytes(h, n, k);
     st = ensure_workspace(h, need);
     if (st != MF_OK) return st;
     return cuda_status(launch_signal(h, (const uint32_t*)x, n, k, dtype == MF_FLOAT32,
@@ -179,7 +204,7 @@ mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
     const size_t io = xb + yb + (argmed_host ? yb : 0);
-    const size_t need = signal_workspace_bytes(n, k);
+    const size_t need = signal_workspace_bytes(h, n, k);
     st = ensure_workspace(h, io + need);
     if (st != MF_OK) return st;
     char* base = (char*)h->ws;
@@ -230,21 +255,16 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
     // the large-k ones follow one by one, reusing the same workspace
     std::vector<int64_t> xo, nn, yo;
     std::vector<int32_t> kk, big;
-    const int kmax_pipe = mf::pipeline_max_k();
-    size_t big_need = 0;
     for (int32_t s = 0; s < nseg; ++s) {
-        if (segs[s].k > kmax_pipe) {
+        if (use_large(h, segs[s].k)) {
             big.push_back(s);
-            big_need = std::max(big_need, mf::large_workspace_bytes(segs[s].n, segs[s].k));
             continue;
         }
         xo.push_back(segs[s].x_off); nn.push_back(segs[s].n);
         yo.push_back(segs[s].y_off); kk.push_back(segs[s].k);
     }
     const int32_t nsmall = (int32_t)kk.size();
-    const size_t small_need =
-        nsmall ? mf::pipeline_batched_workspace_bytes(nn.data(), kk.data(), nsmall) : 0;
-    const size_t need = std::max(small_need, big_need);
+    const size_t need = batched_need(h, segs, nseg);
     mf_status st = ensure_workspace(h, need);
     if (st != MF_OK) return st;
     const bool is_float = dtype == MF_FLOAT32;
@@ -332,6 +352,52 @@ mf_status mf_set_tuning(mf_handle h, int32_t k, int32_t sort_pairs_per_cta, int3
     mf::Tuning& t = h->tune[mf::tune_class_of(k)];
     t.sort_G = sort_pairs_per_cta > 0 ? sort_pairs_per_cta : 0;
     t.epi_G = store_pairs_per_cta > 0 ? store_pairs_per_cta : 0;
+    return MF_OK;
+}
+
+mf_status mf_batched_workspace_bytes(mf_handle h, const mf_segment* segs, int32_t nseg,
+                                     size_t* bytes) {
+    if (!h || !bytes || (!segs && nseg > 0)) return MF_ERR_NULL;
+    if (nseg < 0) return MF_ERR_BAD_SEGMENT;
+    for (int32_t s = 0; s < nseg; ++s) {
+        const mf_segment& d = segs[s];
+        if (d.pad != 0 || d.n < 1 || d.k < 1 || d.k % 2 == 0 || (int64_t)d.k > d.n || d.k > h->max_k)
+            return MF_ERR_BAD_SEGMENT;
+    }
+    *bytes = batched_need(h, segs, nseg);
+    return MF_OK;
+}
+
+mf_status mf_workspace_size(mf_handle h, size_t* bytes) {
+    if (!h || !bytes) return MF_ERR_NULL;
+    *bytes = h->ws_size;
+    return MF_OK;
+}
+
+mf_status mf_release_workspace(mf_handle h) {
+    if (!h) return MF_ERR_NULL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return MF_ERR_CUDA;
+    if (capturing(h->stream)) return MF_ERR_UNSUPPORTED;
+    if (!h->ws) return MF_OK;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return MF_ERR_CUDA;
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_size = 0;
+    return MF_OK;
+}
+
+mf_status mf_set_tier_threshold(mf_handle h, int32_t k) {
+    if (!h) return MF_ERR_NULL;
+    if (k < 0) return MF_ERR_K_GT_N;
+    const int lim = mf::pipeline_max_k() + 1;
+    h->large_from_k = k == 0 ? std::min(mf::kLargeFromK, lim) : std::min(k, lim);
+    return MF_OK;
+}
+
+mf_status mf_get_tier_threshold(mf_handle h, int32_t* k) {
+    if (!h || !k) return MF_ERR_NULL;
+    *k = h->large_from_k;
     return MF_OK;
 }
 

@@ -91,9 +91,13 @@ cudaError_t launch_pipeline_batched(const uint32_t* x, uint32_t* y, int32_t* arg
                                     cudaStream_t stream, LaunchStats* stats);
 
 // ---- large-k tier (mf_large.cu): pipeline_max_k() < k <= kLargeMaxK -------
-constexpr int kLargeMaxK = (1 << 20) - 1;
+constexpr int kLargeMaxK = (1 << 18) - 1;      // window-rank bitsets fit in shared memory
 constexpr int kLargeSegSteps = 1024;   // target steps per chain segment
 constexpr int kLargeMaxSegs = 32;      // segments per block pair at most
+// Default tier crossover: on GB300 (n = 10^7, random-walk and uniform
+// float32) the large-k tier is faster than the shared-memory pipeline from
+// k of about 5000 (4095: 4.4 vs 5.6 ms; 6001: 7.2 vs 5.9 ms).
+constexpr int kLargeFromK = 5001;
 size_t large_workspace_bytes(int64_t n, int k);
 cudaError_t large_setup();
 cudaError_t launch_large(const uint32_t* x, int64_t n, int k, bool is_float, uint32_t* y,

@@ -12,12 +12,15 @@
 //                     run covers the block, left run first on equal keys
 //   large_ranks       rank of each position in its block
 //   large_jrank       joint ranks of each pair by binary search in the other
-//                     block; M = the pair's merged order, jb = B's ranks
+//                     block: ja / jb by position and M = the merged order
 //   large_unwind      unwind(B)'s links (Section 4: after unwind, undelete(B, i)
 //                     relinks i between its nearest smaller and larger
-//                     elements among positions < i), by a rank bitset per run
-//   large_seginit     rebuilds the state before step i0 of a pair (Section 5.3
-//                     invariant: S_A u S_B are the h smallest of the window)
+//                     elements among positions < i); one CTA per run of
+//                     positions, seeded with a rank bitset of the positions
+//                     before the run
+//   large_seginit     rebuilds the lists before step i0 of a pair (Section
+//                     5.3 invariant: S_A u S_B are the h smallest of the
+//                     window) from bitsets of the window's joint ranks
 //   large_chain       the steps i0 .. i1-1 of Section 5.2 from that state,
 //                     one thread per (pair, segment), lists in global memory
 //   large_epilogue    node -> input element, y / argmed
@@ -25,7 +28,8 @@
 // The serial depth of one pair is k steps; splitting the k steps of a pair
 // into S independent segments, each starting from a state rebuilt with O(k)
 // parallel work, cuts the depth to k / S at the price of S private copies of
-// the pair's lists.
+// the pair's links (8 bytes per node; joint ranks stay in shared per-pair
+// arrays because a node's rank only depends on which block it holds).
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "mf_device.cuh"
@@ -34,6 +38,7 @@
 namespace mf {
 
 constexpr int kChunk = 1024;                     // elements per warp sort
+constexpr int kUnwindRun = 1024;                 // positions per unwind CTA
 constexpr uint32_t kBFlag = 0x80000000u;          // node id of B's element
 constexpr uint32_t kInf = 0xffffffffu;           // joint rank of the sentinels
 
@@ -50,16 +55,65 @@ struct LargeParams {
     uint32_t *keyA, *valA, *keyB, *valB;         // [nblocks][kp] sort ping-pong
     uint32_t* rnk;                               // [nblocks][kp] rank of position p
     uint2* ulink;                                // [nblocks][kp] unwind (prev, next), sentinel k+1
+    uint32_t* ja;                                // [npairs][kp] joint rank of A's position p
     uint32_t* jb;                                // [npairs][kp] joint rank of B's position p
     uint32_t* M;                                 // [npairs][2 kp] node at joint rank r
     uint32_t* out;                               // [npairs][kp] printed node at step i
     int4* seg;                                   // [npairs][S] (mA, mB, sA, sB) before step i0
-    uint32_t* lists;                             // [npairs][S][3][LS] next, prev, joint rank
+    uint2* lists;                                // [npairs][S][LS] (next, prev) per node
 };
 
 __device__ __forceinline__ int block_len(const LargeParams& p, int64_t b) {
     const int64_t r = p.n - b * (int64_t)p.k;
     return (int)(r < p.k ? r : p.k);
+}
+
+// Two-level bitsets in shared memory: W[w] bit b = element 32w+b, summary
+// W1[s] bit c set iff W[32s+c] != 0.
+__device__ __forceinline__ int bits_first_from(const uint32_t* W, const uint32_t* W1,
+                                               int nw, int ns, int r)
+{
+    if (r < 0) r = 0;
+    const int w = r >> 5;
+    if (w >= nw) return -1;
+    const uint32_t m = W[w] & (0xffffffffu << (r & 31));
+    if (m) return (w << 5) + __ffs(m) - 1;
+    const int w1 = w + 1;
+    if (w1 >= nw) return -1;
+    int s = w1 >> 5;
+    uint32_t sm = W1[s] & (0xffffffffu << (w1 & 31));
+    while (true) {
+        if (sm) {
+            const int ww = (s << 5) + __ffs(sm) - 1;
+            return (ww << 5) + __ffs(W[ww]) - 1;
+        }
+        if (++s >= ns) return -1;
+        sm = W1[s];
+    }
+}
+
+// largest element < r, or -1
+__device__ __forceinline__ int bits_last_before(const uint32_t* W, const uint32_t* W1,
+                                                int nw, int r)
+{
+    if (r > (nw << 5)) r = nw << 5;
+    if (r <= 0) return -1;
+    const int t = r - 1;
+    const int w = t >> 5;
+    const uint32_t m = W[w] & (0xffffffffu >> (31 - (t & 31)));
+    if (m) return (w << 5) + 31 - __clz(m);
+    const int w1 = w - 1;
+    if (w1 < 0) return -1;
+    int s = w1 >> 5;
+    uint32_t sm = W1[s] & (0xffffffffu >> (31 - (w1 & 31)));
+    while (true) {
+        if (sm) {
+            const int ww = (s << 5) + 31 - __clz(sm);
+            return (ww << 5) + 31 - __clz(W[ww]);
+        }
+        if (--s < 0) return -1;
+        sm = W1[s];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -152,7 +206,9 @@ large_jrank(LargeParams p, const uint32_t* __restrict__ ks, const uint32_t* __re
         const uint32_t key = ks[abase + e];
         int lo = 0, hi = NB;
         while (lo < hi) { const int mid = (lo + hi) >> 1; if (ks[bbase + mid] < key) lo = mid + 1; else hi = mid; }
-        M[e + lo] = vs[abase + e];
+        const uint32_t pos = vs[abase + e];
+        M[e + lo] = pos;
+        p.ja[q * p.kp + pos] = (uint32_t)(e + lo);
     } else if (e >= (int)p.kp && e - (int)p.kp < NB) {
         const int u = e - (int)p.kp;
         const uint32_t key = ks[bbase + u];
@@ -164,151 +220,189 @@ large_jrank(LargeParams p, const uint32_t* __restrict__ ks, const uint32_t* __re
     }
 }
 
-// unwind links of block b >= 1, lane = run of positions [i0, i1): the run's
-// bitset starts with the ranks of all positions < i0; for each position, the
-// nearest set ranks below and above its own give (prev, next)
-__global__ void __launch_bounds__(64)
-large_unwind(LargeParams p, const uint32_t* __restrict__ vs, int seglen, int nw, int ns)
+// Unwind links of block b >= 1 (blockIdx.x = b - 1), positions
+// [i0, i0 + kUnwindRun) (blockIdx.y = run).  The bitset of the ranks of all
+// positions < i0 is built from the sorted order; then one thread inserts the
+// run's ranks in position order, recording for each its nearest set ranks
+// below and above; the CTA turns those ranks into nodes.
+__global__ void __launch_bounds__(256)
+large_unwind(LargeParams p, const uint32_t* __restrict__ vs, int nw, int ns)
 {
     extern __shared__ __align__(16) uint32_t sw[];
-    const int lane = threadIdx.x, S = blockDim.x;
-    const int64_t b = 1 + blockIdx.x;
-    if (b >= p.nblocks) return;
+    const int64_t b = 1 + (int64_t)blockIdx.x;
     const int NB = block_len(p, b);
-    const int i0 = lane * seglen, i1 = min(i0 + seglen, NB);
-    if (i0 >= i1) return;
-    uint32_t* W0 = sw + lane;                     // word x at W0[x * S]
-    uint32_t* W1 = sw + (size_t)nw * S + lane;
-    for (int w = 0; w < nw; ++w) W0[(size_t)w * S] = 0u;
-    for (int s = 0; s < ns; ++s) W1[(size_t)s * S] = 0u;
+    const int i0 = blockIdx.y * kUnwindRun;
+    if (i0 >= NB) return;
+    const int len = min(kUnwindRun, NB - i0);
+    int2* pp = reinterpret_cast<int2*>(sw);       // kUnwindRun (pred, succ) ranks
+    uint32_t* rr = sw + 2 * kUnwindRun;            // kUnwindRun ranks of the run
+    uint32_t* W = rr + kUnwindRun;                 // nw words
+    uint32_t* W1 = W + nw;                         // ns words
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int64_t base = b * p.kp;
-    const uint32_t* rk = p.rnk + base;
-    for (int i = 0; i < i0; ++i) {
-        const uint32_t r = rk[i];
-        W0[(size_t)(r >> 5) * S] |= 1u << (r & 31);
-        W1[(size_t)(r >> 10) * S] |= 1u << ((r >> 5) & 31);
+    for (int w = warp; w < nw; w += nwarp) {
+        const int r = (w << 5) + lane;
+        const bool set = r < NB && (int)__ldg(vs + base + r) < i0;
+        const uint32_t word = __ballot_sync(kFull, set);
+        if (lane == 0) W[w] = word;
     }
+    for (int t = threadIdx.x; t < len; t += blockDim.x) rr[t] = __ldg(p.rnk + base + i0 + t);
+    __syncthreads();
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        uint32_t sm = 0;
+        for (int c = 0; c < 32 && (s << 5) + c < nw; ++c)
+            if (W[(s << 5) + c]) sm |= 1u << c;
+        W1[s] = sm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int t = 0; t < len; ++t) {
+            const int r = (int)rr[t];
+            pp[t] = make_int2(bits_last_before(W, W1, nw, r), bits_first_from(W, W1, nw, ns, r + 1));
+            W[r >> 5] |= 1u << (r & 31);
+            W1[r >> 10] |= 1u << ((r >> 5) & 31);
+        }
+    }
+    __syncthreads();
     const uint32_t sentB = (uint32_t)p.k + 1;
-    for (int i = i0; i < i1; ++i) {
-        const int r = (int)rk[i];
-        const int w = r >> 5, bb = r & 31;
-        const uint32_t word = W0[(size_t)w * S];
-        int pred = -1, succ = -1;
-        const uint32_t mlo = word & ((1u << bb) - 1u);
-        const uint32_t mhi = word & ~((2u << bb) - 1u);
-        if (mlo) {
-            pred = (w << 5) | (31 - __clz(mlo));
-        } else {
-            int s = w >> 5;
-            uint32_t sm = W1[(size_t)s * S] & ((1u << (w & 31)) - 1u);
-            while (true) {
-                if (sm) {
-                    const int ww = (s << 5) | (31 - __clz(sm));
-                    pred = (ww << 5) | (31 - __clz(W0[(size_t)ww * S]));
-                    break;
-                }
-                if (--s < 0) break;
-                sm = W1[(size_t)s * S];
-            }
-        }
-        if (mhi) {
-            succ = (w << 5) | (__ffs(mhi) - 1);
-        } else {
-            int s = w >> 5;
-            uint32_t sm = W1[(size_t)s * S] & ~((2u << (w & 31)) - 1u);
-            while (true) {
-                if (sm) {
-                    const int ww = (s << 5) | (__ffs(sm) - 1);
-                    succ = (ww << 5) | (__ffs(W0[(size_t)ww * S]) - 1);
-                    break;
-                }
-                if (++s >= ns) break;
-                sm = W1[(size_t)s * S];
-            }
-        }
-        W0[(size_t)w * S] = word | (1u << bb);
-        W1[(size_t)(w >> 5) * S] |= 1u << (w & 31);
-        const uint32_t pv = pred >= 0 ? vs[base + pred] : sentB;
-        const uint32_t nx = succ >= 0 ? vs[base + succ] : sentB;
-        p.ulink[base + i] = make_uint2(pv, nx);
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+        const int2 q = pp[t];
+        const uint32_t pv = q.x >= 0 ? __ldg(vs + base + q.x) : sentB;
+        const uint32_t nx = q.y >= 0 ? __ldg(vs + base + q.y) : sentB;
+        p.ulink[base + i0 + t] = make_uint2(pv, nx);
     }
 }
 
-// One warp per (pair q, segment s), i0 = s * L: the state before step i0.
-// The window is A's positions >= i0 and B's positions < i0; walking the
-// pair's merged order M, the kept elements of each block come out in sorted
-// order (their links), and the first h kept elements are the small ones.
+// One CTA per (pair q, segment s), i0 = s * L: the lists before step i0.
+// The window is A's positions >= i0 and B's positions < i0.  KA / KB mark
+// the joint ranks of its A and B elements; a node's list neighbours are the
+// nearest marked ranks of its own block, and the small elements are the
+// window's h smallest (Section 5.3 invariant), found by a prefix count.
 __global__ void __launch_bounds__(256)
-large_seginit(LargeParams p)
+large_seginit(LargeParams p, int nw, int ns)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t sid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (sid >= p.npairs * p.S) return;
+    extern __shared__ __align__(16) uint32_t sw[];
+    const int64_t sid = blockIdx.x;
     const int64_t q = sid / p.S;
     const int s = (int)(sid - q * p.S);
     const int NB = block_len(p, q + 1);
     const int i0 = s * p.L;
     if (i0 >= NB) return;
-    const int k = p.k, h = p.h;
+    const int k = p.k, h = p.h, tot = k + NB;
     const uint32_t SA = (uint32_t)k, SB = (uint32_t)k + 1;
-    uint32_t* NX = p.lists + sid * 3 * p.LS;
-    uint32_t* PV = NX + p.LS;
-    uint32_t* JR = PV + p.LS;
+    uint32_t* KA = sw;
+    uint32_t* KB = KA + nw;
+    uint32_t* KA1 = KB + nw;
+    uint32_t* KB1 = KA1 + ns;
+    int* scan = reinterpret_cast<int*>(KB1 + ns); // 2 * blockDim.x
+    int* sh_state = scan + 2 * blockDim.x;        // T, s_A
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const uint32_t* M = p.M + q * 2 * p.kp;
-    const int tot = k + NB;
-    const uint32_t lt = (1u << lane) - 1u;
-    uint32_t lastA = SA, lastB = SB, mA = SA, mB = SB;
-    int wcount = 0, sA = 0, sB = 0;
-    bool foundA = false, foundB = false;
-    for (int r0 = 0; r0 < tot; r0 += 32) {
-        const int r = r0 + lane;
-        const bool valid = r < tot;
-        const uint32_t id = valid ? M[r] : 0u;
+    for (int w = warp; w < nw; w += nwarp) {
+        const int r = (w << 5) + lane;
+        const uint32_t id = r < tot ? __ldg(M + r) : 0u;
         const bool isB = (id & kBFlag) != 0;
         const uint32_t pos = id & ~kBFlag;
-        const bool keepA = valid && !isB && pos >= (uint32_t)i0;
-        const bool keepB = valid && isB && pos < (uint32_t)i0;
-        const uint32_t bA = __ballot_sync(kFull, keepA);
-        const uint32_t bB = __ballot_sync(kFull, keepB);
-        const uint32_t bK = bA | bB;
-        const bool small = wcount + __popc(bK & lt) < h;
-        const uint32_t loA = bA & lt, loB = bB & lt;
-        const uint32_t pA = __shfl_sync(kFull, pos, loA ? 31 - __clz(loA) : lane);
-        const uint32_t pB = __shfl_sync(kFull, pos, loB ? 31 - __clz(loB) : lane);
-        if (keepA) {
-            const uint32_t prev = loA ? pA : lastA;
-            PV[pos] = prev; NX[prev] = pos; JR[pos] = (uint32_t)r;
-        }
-        if (keepB) {
-            const uint32_t prev = loB ? pB : lastB;
-            PV[pos] = prev; NX[prev] = pos; JR[pos] = (uint32_t)r;
-        }
-        const uint32_t smA = __ballot_sync(kFull, keepA && small);
-        const uint32_t smB = __ballot_sync(kFull, keepB && small);
-        sA += __popc(smA);
-        sB += __popc(smB);
-        const uint32_t bigA = bA & ~smA, bigB = bB & ~smB;
-        const uint32_t cA = __shfl_sync(kFull, pos, bigA ? __ffs(bigA) - 1 : 0);
-        const uint32_t cB = __shfl_sync(kFull, pos, bigB ? __ffs(bigB) - 1 : 0);
-        if (!foundA && bigA) { mA = cA; foundA = true; }
-        if (!foundB && bigB) { mB = cB; foundB = true; }
-        const uint32_t tA = __shfl_sync(kFull, pos, bA ? 31 - __clz(bA) : 0);
-        const uint32_t tB = __shfl_sync(kFull, pos, bB ? 31 - __clz(bB) : 0);
-        if (bA) lastA = tA;
-        if (bB) lastB = tB;
-        wcount += __popc(bK);
+        const uint32_t a = __ballot_sync(kFull, r < tot && !isB && pos >= (uint32_t)i0);
+        const uint32_t bb = __ballot_sync(kFull, r < tot && isB && pos < (uint32_t)i0);
+        if (lane == 0) { KA[w] = a; KB[w] = bb; }
     }
-    if (lane == 0) {
-        NX[lastA] = SA; PV[SA] = lastA;
-        NX[lastB] = SB; PV[SB] = lastB;
-        JR[SA] = kInf; JR[SB] = kInf;
-        p.seg[sid] = make_int4((int)mA, (int)mB, sA, sB);
+    __syncthreads();
+    for (int t = threadIdx.x; t < ns; t += blockDim.x) {
+        uint32_t sa = 0, sb = 0;
+        for (int c = 0; c < 32 && (t << 5) + c < nw; ++c) {
+            if (KA[(t << 5) + c]) sa |= 1u << c;
+            if (KB[(t << 5) + c]) sb |= 1u << c;
+        }
+        KA1[t] = sa;
+        KB1[t] = sb;
+    }
+    // window rank h: thread t counts the marks of words [w0, w1)
+    const int per = (nw + blockDim.x - 1) / blockDim.x;
+    const int w0 = min(nw, (int)threadIdx.x * per), w1 = min(nw, w0 + per);
+    int ca = 0, cb = 0;
+    for (int w = w0; w < w1; ++w) { ca += __popc(KA[w]); cb += __popc(KB[w]); }
+    scan[threadIdx.x] = ca + cb;
+    scan[blockDim.x + threadIdx.x] = ca;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0, acca = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            const int c = scan[t], a = scan[blockDim.x + t];
+            scan[t] = acc; scan[blockDim.x + t] = acca;
+            acc += c; acca += a;
+        }
+    }
+    __syncthreads();
+    {
+        int before = scan[threadIdx.x], beforeA = scan[blockDim.x + threadIdx.x];
+        if (before <= h && h < before + ca + cb) {
+            // the element of window rank h lies in this thread's words
+            for (int w = w0; w < w1; ++w) {
+                const uint32_t any = KA[w] | KB[w];
+                const int c = __popc(any);
+                if (before + c > h) {
+                    uint32_t m = any;
+                    for (int j = h - before; j > 0; --j) m &= m - 1;   // drop the lower ones
+                    const int bit = __ffs(m) - 1;
+                    const int T = (w << 5) + bit;
+                    const int sA = beforeA + __popc(KA[w] & ((1u << bit) - 1u));
+                    sh_state[0] = T;
+                    sh_state[1] = sA;
+                    break;
+                }
+                before += c;
+                beforeA += __popc(KA[w]);
+            }
+        }
+    }
+    __syncthreads();
+    uint2* Lq = p.lists + sid * p.LS;
+    const uint32_t* JA = p.ja + q * p.kp;
+    const uint32_t* JB = p.jb + q * p.kp;
+    auto node = [&](int r, uint32_t sent) -> uint32_t {
+        return r >= 0 ? (__ldg(M + r) & ~kBFlag) : sent;
+    };
+    if (threadIdx.x == 0) {
+        const int T = sh_state[0], sA = sh_state[1];
+        const uint32_t mA = node(bits_first_from(KA, KA1, nw, ns, T), SA);
+        const uint32_t mB = node(bits_first_from(KB, KB1, nw, ns, T), SB);
+        p.seg[sid] = make_int4((int)mA, (int)mB, sA, h - sA);
+        Lq[SA] = make_uint2(node(bits_first_from(KA, KA1, nw, ns, 0), SA),
+                            node(bits_last_before(KA, KA1, nw, tot), SA));
+        Lq[SB] = make_uint2(node(bits_first_from(KB, KB1, nw, ns, 0), SB),
+                            node(bits_last_before(KB, KB1, nw, tot), SB));
+    }
+    // each thread handles 4 slots per round so that their global loads overlap
+    constexpr int U = 4;
+    for (int j0 = threadIdx.x; j0 < k; j0 += U * blockDim.x) {
+        int r[U], nx[U], pv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * (int)blockDim.x;
+            r[u] = j < k ? (int)__ldg((j >= i0 ? JA : JB) + j) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * (int)blockDim.x;
+            const bool a = j >= i0;
+            nx[u] = bits_first_from(a ? KA : KB, a ? KA1 : KB1, nw, ns, r[u] + 1);
+            pv[u] = bits_last_before(a ? KA : KB, a ? KA1 : KB1, nw, r[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * (int)blockDim.x;
+            const uint32_t sent = j >= i0 ? SA : SB;
+            const uint2 v = make_uint2(node(nx[u], sent), node(pv[u], sent));
+            if (j < k) Lq[j] = v;
+        }
     }
 }
 
 // Section 5.2, steps i0 .. i1-1 of pair q: delete(A, i), undelete(B, i),
-// advance while s_A + s_B < h, print min(peek A, peek B)
-__global__ void __launch_bounds__(128)
+// advance while s_A + s_B < h, print min(peek A, peek B).  mA is always a
+// node of A's list (joint rank ja) and mB of B's (jb); sentinels rank last.
+__global__ void __launch_bounds__(32)
 large_chain(LargeParams p)
 {
     const int64_t sid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -320,42 +414,55 @@ large_chain(LargeParams p)
     if (i0 >= NB) return;
     const int i1 = min(i0 + p.L, NB);
     const int h = p.h;
-    uint32_t* NX = p.lists + sid * 3 * p.LS;
-    uint32_t* PV = NX + p.LS;
-    uint32_t* JR = PV + p.LS;
+    const uint32_t k = (uint32_t)p.k;
+    uint2* Lq = p.lists + sid * p.LS;
+    uint32_t* NXp = reinterpret_cast<uint32_t*>(Lq);       // next of node j at [2j]
+    const uint32_t* JA = p.ja + q * p.kp;
+    const uint32_t* JB = p.jb + q * p.kp;
+    const uint2* UL = p.ulink + (q + 1) * p.kp;
+    uint32_t* OUT = p.out + q * p.kp;
     const int4 st = p.seg[sid];
     uint32_t mA = (uint32_t)st.x, mB = (uint32_t)st.y;
     int sA = st.z, sB = st.w;
-    const uint2* UL = p.ulink + (q + 1) * p.kp;
-    const uint32_t* JB = p.jb + q * p.kp;
-    uint32_t* OUT = p.out + q * p.kp;
+    uint32_t jmA = mA < k ? __ldg(JA + mA) : kInf;
+    uint32_t jmB = mB < k ? __ldg(JB + mB) : kInf;
+    uint32_t ra = __ldg(JA + i0), rb = __ldg(JB + i0);
+    uint2 u = __ldg(UL + i0);
     for (int i = i0; i < i1; ++i) {
         const uint32_t ui = (uint32_t)i;
-        // delete(A, i)
-        const uint32_t pa = PV[i], na = NX[i], ra = JR[i];
-        const bool was_small = ra < JR[mA];
-        NX[pa] = na;
-        PV[na] = pa;
-        if (was_small) {
+        const uint2 Li = Lq[i];
+        const uint2 LmA = Lq[mA];
+        const uint2 LmB = Lq[mB];
+        uint32_t ra_n = 0, rb_n = 0;
+        uint2 u_n = make_uint2(0, 0);
+        if (i + 1 < i1) { ra_n = __ldg(JA + i + 1); rb_n = __ldg(JB + i + 1); u_n = __ldg(UL + i + 1); }
+        // delete(A, i): unlink, then keep s_A and m consistent
+        const uint32_t na = Li.x, pa = Li.y;
+        NXp[2 * pa] = na;
+        NXp[2 * na + 1] = pa;
+        if (ra < jmA) {
             --sA;
         } else {
-            if (mA == ui) mA = na;
-            if (sA > 0) { mA = PV[mA]; --sA; }
+            uint32_t pvm = (mA == na) ? pa : LmA.y;        // prev of m after the unlink
+            if (mA == ui) { mA = na; pvm = pa; }
+            if (sA > 0) { mA = pvm; --sA; }
+            jmA = mA < k ? __ldg(JA + mA) : kInf;
         }
         // undelete(B, i): slot i now holds B's element i
-        const uint2 u = UL[i];
-        const uint32_t rb = JB[i];
-        PV[i] = u.x; NX[i] = u.y; JR[i] = rb;
-        NX[u.x] = ui;
-        PV[u.y] = ui;
-        if (rb < JR[mB]) mB = PV[mB];
-        // advance the smaller peek while s_A + s_B < h
-        uint32_t jA = JR[mA], jB = JR[mB];
-        if (sA + sB < h) {
-            if (jA < jB) { mA = NX[mA]; ++sA; jA = JR[mA]; }
-            else         { mB = NX[mB]; ++sB; jB = JR[mB]; }
+        Lq[i] = make_uint2(u.y, u.x);
+        NXp[2 * u.x] = ui;
+        NXp[2 * u.y + 1] = ui;
+        if (rb < jmB) {
+            mB = (mB == u.y) ? ui : LmB.y;
+            jmB = mB < k ? __ldg(JB + mB) : kInf;
         }
-        OUT[i] = jA < jB ? mA : (kBFlag | mB);
+        // advance the smaller peek while s_A + s_B < h
+        if (sA + sB < h) {
+            if (jmA < jmB) { mA = Lq[mA].x; ++sA; jmA = mA < k ? __ldg(JA + mA) : kInf; }
+            else           { mB = Lq[mB].x; ++sB; jmB = mB < k ? __ldg(JB + mB) : kInf; }
+        }
+        OUT[i] = jmA < jmB ? mA : (kBFlag | mB);
+        ra = ra_n; rb = rb_n; u = u_n;
     }
 }
 
@@ -399,6 +506,20 @@ static LargeShape large_shape(int64_t n, int k)
     return s;
 }
 
+// shared memory of the unwind and segment-init CTAs
+static size_t unwind_smem(int k, int* nw, int* ns)
+{
+    *nw = (k + 31) / 32;
+    *ns = (*nw + 31) / 32;
+    return 4ull * (size_t)(*nw + *ns) + 12ull * kUnwindRun;
+}
+static size_t seginit_smem(int k, int* nw, int* ns)
+{
+    *nw = (2 * k + 31) / 32;
+    *ns = (*nw + 31) / 32;
+    return 8ull * (size_t)(*nw + *ns) + 2 * 4 * 256 + 16;
+}
+
 size_t large_workspace_bytes(int64_t n, int k)
 {
     const LargeShape s = large_shape(n, k);
@@ -406,10 +527,10 @@ size_t large_workspace_bytes(int64_t n, int k)
     const uint64_t np1 = (uint64_t)(s.npairs > 0 ? s.npairs : 1);
     uint64_t b = a256(4ull * nb * kp) * 5;                   // keyA valA keyB valB rnk
     b += a256(8ull * nb * kp);                               // ulink
-    b += a256(4ull * np1 * kp) * 2;                          // jb out
+    b += a256(4ull * np1 * kp) * 3;                          // ja jb out
     b += a256(8ull * np1 * kp);                              // M
     b += a256(16ull * np1 * s.S);                            // seg
-    b += a256(12ull * np1 * s.S * (uint64_t)s.LS);           // lists
+    b += a256(8ull * np1 * s.S * (uint64_t)s.LS);            // lists
     return (size_t)b;
 }
 
@@ -418,7 +539,10 @@ cudaError_t large_setup()
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(large_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(8 * kChunkWarpBytes)))) return e;
-    return cudaFuncSetAttribute(large_unwind, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
+    if ((e = cudaFuncSetAttribute(large_unwind, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kMaxSmemBytes))) return e;
+    return cudaFuncSetAttribute(large_seginit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kMaxSmemBytes);
 }
 
 cudaError_t launch_large(const uint32_t* x, int64_t n, int k, bool is_float, uint32_t* y,
@@ -427,6 +551,10 @@ cudaError_t launch_large(const uint32_t* x, int64_t n, int k, bool is_float, uin
 {
     if (k < 1 || (k & 1) == 0 || k > kLargeMaxK || n < k) return cudaErrorInvalidValue;
     if (ws_bytes < large_workspace_bytes(n, k)) return cudaErrorInvalidValue;
+    int unw, uns, snw, sns;
+    const size_t usmem = unwind_smem(k, &unw, &uns);
+    const size_t ssmem = seginit_smem(k, &snw, &sns);
+    if (usmem > (size_t)kMaxSmemBytes || ssmem > (size_t)kMaxSmemBytes) return cudaErrorInvalidValue;
     const LargeShape sh = large_shape(n, k);
     LargeParams p{};
     p.x = x; p.y = y; p.argmed = argmed;
@@ -443,11 +571,12 @@ cudaError_t launch_large(const uint32_t* x, int64_t n, int k, bool is_float, uin
     p.valB = (uint32_t*)w; w += a256(4ull * nb * kp);
     p.rnk = (uint32_t*)w;  w += a256(4ull * nb * kp);
     p.ulink = (uint2*)w;   w += a256(8ull * nb * kp);
+    p.ja = (uint32_t*)w;   w += a256(4ull * np1 * kp);
     p.jb = (uint32_t*)w;   w += a256(4ull * np1 * kp);
     p.out = (uint32_t*)w;  w += a256(4ull * np1 * kp);
     p.M = (uint32_t*)w;    w += a256(8ull * np1 * kp);
     p.seg = (int4*)w;      w += a256(16ull * np1 * sh.S);
-    p.lists = (uint32_t*)w;
+    p.lists = (uint2*)w;
     auto launched = [&]() -> cudaError_t {
         if (stats) stats->launches += 1;
         return cudaGetLastError();
@@ -475,17 +604,13 @@ cudaError_t launch_large(const uint32_t* x, int64_t n, int k, bool is_float, uin
         const int64_t tj = sh.npairs * 2 * sh.kp;
         large_jrank<<<(unsigned)((tj + 255) / 256), 256, 0, stream>>>(p, ks, vs);
         if ((e = launched()) != cudaSuccess) return e;
-        const int nw = (k + 31) / 32, ns = (nw + 31) / 32;
-        const size_t per_lane = 4ull * (size_t)(nw + ns);
-        int S = (int)((size_t)kMaxSmemBytes / per_lane);
-        S = S > 64 ? 64 : (S < 1 ? 1 : S);
-        const int seglen = (k + S - 1) / S;
-        large_unwind<<<(unsigned)(sh.nblocks - 1), S, per_lane * S, stream>>>(p, vs, seglen, nw, ns);
+        const dim3 ug((unsigned)(sh.nblocks - 1), (unsigned)((k + kUnwindRun - 1) / kUnwindRun));
+        large_unwind<<<ug, 256, usmem, stream>>>(p, vs, unw, uns);
         if ((e = launched()) != cudaSuccess) return e;
         const int64_t nseg = sh.npairs * sh.S;
-        large_seginit<<<(unsigned)((nseg * 32 + 255) / 256), 256, 0, stream>>>(p);
+        large_seginit<<<(unsigned)nseg, 256, ssmem, stream>>>(p, snw, sns);
         if ((e = launched()) != cudaSuccess) return e;
-        large_chain<<<(unsigned)((nseg + 127) / 128), 128, 0, stream>>>(p);
+        large_chain<<<(unsigned)((nseg + 31) / 32), 32, 0, stream>>>(p);
         if ((e = launched()) != cudaSuccess) return e;
     }
     const int64_t m = n - k + 1;

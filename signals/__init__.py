@@ -19,9 +19,14 @@ configurations this library is measured on:
 * ``distinct_f32``     -- permutation of 0..n-1 scaled by 1e-3 plus N(0, 0.1),
                           redrawn until all values are distinct
 * ``serving_requests`` -- Poisson arrivals with log-uniform n and k
+* ``request_payload``  -- one served request's samples from SplitMix64
 
 All generators take an explicit integer seed and use numpy's PCG64
-``default_rng``; the default seed is 20140607.
+``default_rng`` -- except the served payloads, which the request server
+draws on the GPU: they follow SplitMix64 (Steele, Lea and Flood, "Fast
+splittable pseudorandom number generators", OOPSLA 2014), a counter-based
+generator that the device code implements from the same published
+definition, so both sides get identical bits.  The default seed is 20140607.
 """
 from __future__ import annotations
 
@@ -229,9 +234,30 @@ def serving_requests(rate_hz: float = 2000.0, duration_s: float = 60.0,
     return out
 
 
+SPLITMIX_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Outputs offset+1 .. offset+n of the SplitMix64 stream started at state
+    ``seed``: state_i = seed + i * gamma (mod 2^64), then the published
+    finaliser (xor-shift 30, multiply, xor-shift 27, multiply, xor-shift 31)."""
+    i = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * SPLITMIX_GAMMA
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def payload_from_bits(z: np.ndarray, dtype: str) -> np.ndarray:
+    """int32: the top 16 bits (uniform on [0, 65536)); float32: the top 24
+    bits times 2^-24 (uniform on [0, 1), exact in float32)."""
+    if dtype == "int32":
+        return (z >> np.uint64(48)).astype(np.int32)
+    return ((z >> np.uint64(40)).astype(np.float64) * 2.0 ** -24).astype(np.float32)
+
+
 def request_payload(req: Request) -> np.ndarray:
-    """Samples of one served request: int32 U[0, 65536) or float32 U[0, 1)."""
-    rng = _rng(req.seed)
-    if req.dtype == "int32":
-        return rng.integers(0, 65536, size=req.n, dtype=np.int64).astype(np.int32)
-    return rng.random(req.n, dtype=np.float32)
+    """Samples of one served request: int32 U[0, 65536) or float32 U[0, 1),
+    element i from output i+1 of SplitMix64 seeded with the request's seed."""
+    return payload_from_bits(splitmix64(req.seed, req.n), req.dtype)

@@ -25,7 +25,9 @@ def lib():
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "mf.h")).read()
+    inc = os.path.join(ROOT, "include")
+    text = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc))
+                   if f.endswith(".h"))
     return sorted(set(re.findall(r"^\s*(?:mf_status|const char\*)\s+(mf_\w+)\s*\(", text, re.M)))
 
 

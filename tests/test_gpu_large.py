@@ -78,7 +78,7 @@ def check(h, x, k, full=False, seed=0):
         np.testing.assert_array_equal(a[st], ra)
 
 
-@pytest.mark.parametrize("k", [8005, 9001])
+@pytest.mark.parametrize("k", [9345, 10001])
 @pytest.mark.parametrize("kind", ["walk", "i32", "uniform"])
 def test_just_above_pipeline_full(handle, k, kind):
     n = 3 * k + 1234
@@ -101,6 +101,12 @@ def test_serving_range_sampled(handle, k):
     check(handle, random_walk_f32(n, seed=k), k, seed=k)
     xi = np.ascontiguousarray(uniform_i32(n, seed=k + 1) % 65536).astype(np.int32)
     check(handle, xi, k, seed=k + 1)
+
+
+def test_maximum_k(handle):
+    k = (1 << 18) - 1
+    x = uniform_f32(2 * k + 4321, seed=11)
+    check(handle, x, k, seed=11)
 
 
 def test_large_k_ten_million_sampled(handle):
@@ -145,3 +151,44 @@ def test_host_entry_point_large_k(handle):
     yd, ad = gpu_filter(handle, x, k)
     assert np.array_equal(bits(y), bits(yd))
     np.testing.assert_array_equal(a.astype(np.int64), ad)
+
+
+@pytest.fixture(scope="module")
+def large_handle():
+    """A handle that sends every window size to the large-k tier."""
+    mf.load_library()
+    h = mf.mf_create(0, torch.cuda.current_stream(DEV))
+    mf.mf_set_tier_threshold(h, 1)
+    yield h
+    mf.mf_destroy(h)
+
+
+@pytest.mark.parametrize("k", [1, 3, 31, 101, 1001, 1025, 4095])
+@pytest.mark.parametrize("kind", ["walk", "i32_ties", "uniform"])
+def test_large_tier_at_small_k_full(large_handle, k, kind):
+    n = max(5 * k + 13, 3001)
+    x = {"walk": lambda: random_walk_f32(n, seed=k),
+         "i32_ties": lambda: (uniform_i32(n, seed=k) % 7).astype(np.int32),
+         "uniform": lambda: uniform_f32(n, seed=k)}[kind]()
+    check(large_handle, np.ascontiguousarray(x), k, full=True)
+
+
+def test_tiers_agree_and_threshold_resets(handle, large_handle):
+    x = random_walk_f32(300_001, seed=12)
+    for k in (2047, 9343):
+        y1, a1 = gpu_filter(handle, x, k)
+        y2, a2 = gpu_filter(large_handle, x, k)
+        assert np.array_equal(bits(y1), bits(y2))
+        np.testing.assert_array_equal(a1, a2)
+    h = mf.mf_create(0, torch.cuda.current_stream(DEV))
+    try:
+        mf.mf_set_tier_threshold(h, 101)
+        mf.mf_set_tier_threshold(h, 0)
+        l0 = mf.mf_launch_count(h)
+        gpu_filter(h, x, 1001)
+        assert mf.mf_launch_count(h) - l0 == 4          # the four pipeline kernels
+        l0 = mf.mf_launch_count(h)
+        gpu_filter(h, x, 6001)                           # default crossover: large-k tier
+        assert mf.mf_launch_count(h) - l0 > 4
+    finally:
+        mf.mf_destroy(h)

@@ -158,10 +158,10 @@ def test_full_size_k1001_sampled(handle, kind):
 
 
 def test_max_supported_k_and_unsupported(handle):
-    """k up to 2^20 - 1 is served (large k by the global-memory tier); above it
+    """k up to 2^18 - 1 is served (large k by the global-memory tier); above it
     the call is refused with MF_ERR_UNSUPPORTED before any work."""
     lib = mf.load_library()
-    k = (1 << 20) + 1
+    k = (1 << 18) + 1
     xd = torch.zeros(k + 2, device=DEV)
     yd = torch.empty(3, device=DEV)
     assert lib.mf_filter(handle, 1, xd.data_ptr(), k + 2, k, yd.data_ptr(), None) == 8

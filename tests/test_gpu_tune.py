@@ -18,7 +18,7 @@ DEV = torch.device("cuda:0")
 def test_autotune_one_class_and_reload(tmp_path):
     h = mf.mf_create(0, torch.cuda.current_stream(DEV))
     try:
-        res = tune.autotune(h, n=1 << 18, classes=(255,))
+        res = tune.autotune(h, n=1 << 18, classes=(255,), tier=False)
         assert set(res) == {"255"}
         g = res["255"]["sort_pairs_per_cta"]
         assert g in tune.SORT_CANDIDATES
@@ -53,5 +53,30 @@ def test_every_sort_plan_is_exact(g):
         mf.mf_sync(h)
         ry, _ = oracle.median_filter(x_np, 1001)
         np.testing.assert_array_equal(y.cpu().numpy().view(np.uint32), ry.view(np.uint32))
+    finally:
+        mf.mf_destroy(h)
+
+
+def test_tier_threshold_tuning_and_reload(tmp_path):
+    h = mf.mf_create(0, torch.cuda.current_stream(DEV))
+    try:
+        x_np = random_walk_f32(1 << 20, seed=8)
+        x = torch.from_numpy(x_np).to(DEV)
+        res = tune.tune_tier_threshold(h, x, ks=(4095, 9343))
+        assert res["threshold"] in (4095, 9343, tune.PIPELINE_ONLY)
+        assert set(res["ms"]) == {"4095", "9343"}
+        path = tune.save({"tier": res}, str(tmp_path / "tier.json"))
+        h2 = mf.mf_create(0, torch.cuda.current_stream(DEV))
+        try:
+            assert tune.load(h2, path)
+            xs = x_np[:40_000]
+            xd = torch.from_numpy(xs).to(DEV)
+            y = torch.empty(xs.size - 9343 + 1, device=DEV)
+            mf.mf_filter(h2, xd, 9343, y)
+            mf.mf_sync(h2)
+            ry, _ = oracle.median_filter(xs, 9343)
+            np.testing.assert_array_equal(y.cpu().numpy().view(np.uint32), ry.view(np.uint32))
+        finally:
+            mf.mf_destroy(h2)
     finally:
         mf.mf_destroy(h)
