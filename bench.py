@@ -320,6 +320,9 @@ def run_ours(args):
 
     batched = None if args.skip_extra else bench_batched(mf, h, dev, stream, seed, args)
     gradient = None if args.skip_extra else bench_gradient(dev, stream, seed, args)
+    serving = None
+    if not args.skip_extra and ws == 1 and args.serve_seconds > 0:
+        serving = bench_serving(dev, DEFAULT_SEED, args)
 
     peak, peak_kind = peaks()
     alg_bytes = 4 * N_SIG + 4 * m
@@ -339,7 +342,9 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_SIG, "k": k, "signal_dtype": "float32",
                    "seed": DEFAULT_SEED, "per_rank": "independent signal (seed + rank)",
-                   "l2": "inputs larger than L2 (268 MB input vs 129 MB L2), no flush",
+                   "l2": (f"inputs larger than L2 ({4 * N_SIG / 1e6:.0f} MB input vs 129 MB L2), "
+                          "no flush") if 4 * N_SIG > 129e6 else
+                         f"input {4 * N_SIG / 1e6:.0f} MB fits in L2: profiling size only",
                    "parallelism": f"replicas x{ws}"},
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "int32_uniform": {"value": value_int, "unit": UNIT,
@@ -357,6 +362,7 @@ def run_ours(args):
         "kernels_ms": kt,
         "batched": batched,
         "gradient": gradient,
+        "serving": serving,
         "clocks": clocks,
         "gpu_launches": launches,
         "cpu_baseline": cpu,
@@ -424,6 +430,30 @@ def bench_batched(mf, h, dev, stream, seed, args):
             "speedup_vs_per_signal": loop_ms / graph_ms}
 
 
+def bench_serving(dev, seed, args):
+    """Poisson arrivals at 2000 requests/s (n log-uniform [1e3, 1e7], odd k
+    log-uniform [3, 100001], int32 or float32 payloads drawn on the device),
+    served with continuous batching on 8 streams under a 40 GB device-memory
+    budget; the first seconds of the same trace also through a per-request
+    server (one stream, one request per call) for comparison."""
+    from paper_1406_1717_gb300 import serve
+    from signals import serving_requests
+    reqs = serving_requests(duration_s=args.serve_seconds, seed=seed)
+    offered = sum(r.n - r.k + 1 for r in reqs) / args.serve_seconds / 1e9
+    rep = serve.run_trace(reqs, slots=8, budget_bytes=serve.DEFAULT_BUDGET, device=dev.index)
+    out = {"workload": f"Poisson 2000 req/s for {args.serve_seconds:g} s, n log-uniform "
+                       "[1e3, 1e7], odd k log-uniform [3, 100001], int32 U[0,65536) or float32 "
+                       "U[0,1) (SplitMix64 on the device), budget 40 GB, 8 streams",
+           "offered_gsamples_per_s": offered, "unit": UNIT, "continuous": rep.summary()}
+    cut = min(args.serve_seconds, args.serve_baseline_seconds)
+    if cut > 0:
+        head = [r for r in reqs if r.arrival_s < cut]
+        per = serve.run_trace(head, slots=1, budget_bytes=serve.DEFAULT_BUDGET,
+                              device=dev.index, max_batch_jobs=1, max_large_jobs=1)
+        out["per_request_first_seconds"] = {"seconds": cut, **per.summary()}
+    return out
+
+
 def bench_gradient(dev, stream, seed, args):
     """Forward (with argmedian) and backward of 64 float32 signals, n = 65536,
     k = 63, distinct values, upstream gradient N(0, 1)."""
@@ -461,10 +491,24 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-windows", type=int, default=100_000)
     ap.add_argument("--skip-extra", action="store_true",
-                    help="skip the batched and gradient configurations")
+                    help="skip the batched, gradient and serving configurations")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the served request trace (0 = skip)")
+    ap.add_argument("--serve-baseline-seconds", type=float, default=10.0,
+                    help="first seconds of the trace also served one request at a time")
+    ap.add_argument("--n", type=int, default=0,
+                    help="signal length override for profiling captures (default 2^26)")
+    ap.add_argument("--k", type=int, default=0,
+                    help="window override for profiling captures (default 1001)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.n or args.k:
+        global N_SIG, K_WIN, WORKLOAD
+        N_SIG = args.n or N_SIG
+        K_WIN = args.k or K_WIN
+        WORKLOAD = (f"float32 Gaussian random walk, n={N_SIG}, k={K_WIN} "
+                    "(size override, not the headline workload)")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -61,8 +61,9 @@ typedef enum {
     MF_ERR_OVERLAP = 9,      /* an output buffer overlaps an input buffer           */
     MF_ERR_DEVICE = 10,      /* device index invalid or not an sm_103 GPU           */
     MF_ERR_BAD_SEGMENT = 11, /* a batched segment descriptor is invalid             */
-    MF_ERR_TOO_LARGE = 12    /* request needs more scratch than mf_filter_noalloc's
+    MF_ERR_TOO_LARGE = 12,   /* request needs more scratch than mf_filter_noalloc's
                                 fixed array holds                                   */
+    MF_ERR_BAD_RANK = 13     /* mf_filter_rank: rank outside 0 .. k-1               */
 } mf_status;
 
 typedef enum { MF_INT32 = 0, MF_FLOAT32 = 1 } mf_dtype;
@@ -107,6 +108,19 @@ mf_status mf_set_stream(mf_handle h, void* cuda_stream);
  * MF_ERR_CUDA (launch failed). */
 mf_status mf_filter(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32_t k,
                     void* y, int32_t* argmed);
+
+/* Rank (order-statistic) filter: y[i] = the element of 0-based rank `rank`
+ * among x[i .. i+k-1] under the (value, index) order of mf_filter, for
+ * i = 0 .. n-k; argmed[i] its index.  The paper's method works unchanged for
+ * any rank h in 0 .. k-1: the post-processing invariant (Section 5.3) keeps
+ * the h smallest elements of the window "small" and prints the smallest
+ * large one.  rank = (k-1)/2 with odd k is mf_filter; any k >= 1 is accepted
+ * here, so even k gives the lower median with rank = k/2 - 1 (the upper
+ * median with k/2), rank 0 a running minimum and rank k-1 a running maximum.
+ * Arguments, ownership, limits and errors as mf_filter, plus MF_ERR_BAD_RANK;
+ * MF_ERR_EVEN_K is never returned. */
+mf_status mf_filter_rank(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32_t k,
+                         int32_t rank, void* y, int32_t* argmed);
 
 /* Same as mf_filter, but x, y and argmed are HOST pointers.  The call copies
  * x to the handle's device workspace, filters, copies y (and argmed) back and
@@ -215,8 +229,10 @@ mf_status mf_get_tier_threshold(mf_handle h, int32_t* k_large_from);
 
 /* Per-kernel timing for measurement.  With timing enabled, every mf_filter /
  * mf_filter_host call records CUDA events on the handle's stream around its
- * four kernels (sort+merge, unwind, post-processing chains, store), in a ring
- * of the last 128 calls; enabling resets the ring. */
+ * four kernel groups (sort+merge, unwind, post-processing chains, store; on
+ * the large-k tier: chunk sort, merge tiers and joint ranks / unwind /
+ * segment states and chains / store), in a ring of the last 128 calls;
+ * enabling resets the ring. */
 mf_status mf_set_timing(mf_handle h, int enable);
 
 /* Sum of each kernel's duration (ms) over the last `ncalls` timed calls

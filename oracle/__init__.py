@@ -64,6 +64,15 @@ def _load():
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
             lib.mfo_windows.restype = ctypes.c_int
+            lib.mfo_rank_filter.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int]
+            lib.mfo_rank_filter.restype = ctypes.c_int
+            lib.mfo_rank_windows.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_int]
+            lib.mfo_rank_windows.restype = ctypes.c_int
             lib.mfo_max_threads.argtypes = []
             lib.mfo_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -114,6 +123,40 @@ def window_medians(x: np.ndarray, k: int, starts, nthreads: int = 0):
                              starts.size, y.ctypes.data, arg.ctypes.data, nthreads)
     if rc != 0:
         raise ValueError(f"mfo_windows returned {rc}")
+    return y, arg
+
+
+def rank_filter(x: np.ndarray, k: int, r: int, nthreads: int = 0):
+    """y[i] = element of 0-based rank r in x[i .. i+k-1] (any k >= 1); (y, arg).
+
+    The median of an odd window is r = (k-1)/2; the lower median of an even
+    window r = k/2 - 1."""
+    x = np.ascontiguousarray(x)
+    code = _dtype_code(x)
+    n = x.size
+    if k < 1 or k > n or not 0 <= r < k:
+        raise ValueError(f"need 1 <= k <= n and 0 <= r < k, got n={n} k={k} r={r}")
+    m = n - k + 1
+    y = np.empty(m, dtype=x.dtype)
+    arg = np.empty(m, dtype=np.int64)
+    rc = _load().mfo_rank_filter(code, x.ctypes.data, n, k, r, y.ctypes.data, arg.ctypes.data,
+                                 nthreads)
+    if rc != 0:
+        raise ValueError(f"mfo_rank_filter returned {rc}")
+    return y, arg
+
+
+def rank_windows(x: np.ndarray, k: int, r: int, starts, nthreads: int = 0):
+    """Rank-r elements of the windows x[s .. s+k-1] for each s in ``starts``."""
+    x = np.ascontiguousarray(x)
+    code = _dtype_code(x)
+    starts = np.ascontiguousarray(np.asarray(starts, dtype=np.int64))
+    y = np.empty(starts.size, dtype=x.dtype)
+    arg = np.empty(starts.size, dtype=np.int64)
+    rc = _load().mfo_rank_windows(code, x.ctypes.data, x.size, k, r, starts.ctypes.data,
+                                  starts.size, y.ctypes.data, arg.ctypes.data, nthreads)
+    if rc != 0:
+        raise ValueError(f"mfo_rank_windows returned {rc}")
     return y, arg
 
 

@@ -36,6 +36,12 @@
  * Method, per window: copy the k (value, index) pairs, sort them with the C
  * library's qsort under the order above, output the element at rank h.  That
  * is O(n k log k): slow and plain on purpose.
+ *
+ * Rank filter (mfo_rank_filter / mfo_rank_windows): the same per-window sort,
+ * output the element at a given 0-based rank r, 0 <= r < k, for any k >= 1.
+ * The paper defines the median for odd k = 2h + 1 (Section 1, Section 3);
+ * for even k the lower median is the element of rank k/2 - 1 (the k/2-th
+ * smallest), the upper median that of rank k/2.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -88,8 +94,9 @@ static int cmp_float32(const void* pa, const void* pb)
     return a->index < b->index ? -1 : (a->index > b->index ? 1 : 0);
 }
 
-/* Median of the window that starts at x[start]; scratch holds k elements. */
-static void window_median(int dtype, const uint32_t* x, int64_t start, int32_t k,
+/* Element of rank r of the window that starts at x[start]; scratch holds k
+ * elements. */
+static void window_select(int dtype, const uint32_t* x, int64_t start, int32_t k, int32_t r,
                           elem_t* scratch, uint32_t* y_out, int64_t* arg_out)
 {
     for (int32_t t = 0; t < k; ++t) {
@@ -97,9 +104,15 @@ static void window_median(int dtype, const uint32_t* x, int64_t start, int32_t k
         scratch[t].index = start + t;
     }
     qsort(scratch, (size_t)k, sizeof(elem_t), dtype == MFO_INT32 ? cmp_int32 : cmp_float32);
-    int32_t h = (k - 1) / 2;
-    *y_out = scratch[h].bits;
-    if (arg_out) *arg_out = scratch[h].index;
+    *y_out = scratch[r].bits;
+    if (arg_out) *arg_out = scratch[r].index;
+}
+
+/* Median (rank h of an odd window k = 2h + 1). */
+static void window_median(int dtype, const uint32_t* x, int64_t start, int32_t k,
+                          elem_t* scratch, uint32_t* y_out, int64_t* arg_out)
+{
+    window_select(dtype, x, start, k, (k - 1) / 2, scratch, y_out, arg_out);
 }
 
 static int check_args(int dtype, const void* x, int64_t n, int32_t k)
@@ -160,6 +173,63 @@ int mfo_windows(int dtype, const uint32_t* x, int64_t n, int32_t k,
 #endif
         for (int64_t j = 0; j < count; ++j)
             window_median(dtype, x, starts[j], k, scratch, &y[j], argmed ? &argmed[j] : NULL);
+        free(scratch);
+    }
+    return 0;
+}
+
+static int check_rank_args(int dtype, const void* x, int64_t n, int32_t k, int32_t r)
+{
+    if (dtype != MFO_INT32 && dtype != MFO_FLOAT32) return -1;
+    if (!x || n < 1) return -2;
+    if (k < 1 || (int64_t)k > n) return -3;
+    if (r < 0 || r >= k) return -5;
+    return 0;
+}
+
+/* Rank filter: y[i] = element of rank r in x[i .. i+k-1], i = 0 .. n-k. */
+int mfo_rank_filter(int dtype, const uint32_t* x, int64_t n, int32_t k, int32_t r,
+                    uint32_t* y, int64_t* arg, int nthreads)
+{
+    int rc = check_rank_args(dtype, x, n, k, r);
+    if (rc) return rc;
+    int64_t m = n - k + 1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        elem_t* scratch = (elem_t*)malloc(sizeof(elem_t) * (size_t)k);
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int64_t i = 0; i < m; ++i)
+            window_select(dtype, x, i, k, r, scratch, &y[i], arg ? &arg[i] : NULL);
+        free(scratch);
+    }
+    return 0;
+}
+
+/* Rank filter on sampled windows (see mfo_windows). */
+int mfo_rank_windows(int dtype, const uint32_t* x, int64_t n, int32_t k, int32_t r,
+                     const int64_t* starts, int64_t count, uint32_t* y, int64_t* arg,
+                     int nthreads)
+{
+    int rc = check_rank_args(dtype, x, n, k, r);
+    if (rc) return rc;
+    for (int64_t j = 0; j < count; ++j)
+        if (starts[j] < 0 || starts[j] > n - k) return -4;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        elem_t* scratch = (elem_t*)malloc(sizeof(elem_t) * (size_t)k);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+        for (int64_t j = 0; j < count; ++j)
+            window_select(dtype, x, starts[j], k, r, scratch, &y[j], arg ? &arg[j] : NULL);
         free(scratch);
     }
     return 0;

@@ -31,7 +31,7 @@ STATUS_NAMES = {
     0: "MF_OK", 1: "MF_ERR_NULL", 2: "MF_ERR_BAD_N", 3: "MF_ERR_EVEN_K",
     4: "MF_ERR_K_GT_N", 5: "MF_ERR_DTYPE", 6: "MF_ERR_OOM", 7: "MF_ERR_CUDA",
     8: "MF_ERR_UNSUPPORTED", 9: "MF_ERR_OVERLAP", 10: "MF_ERR_DEVICE",
-    11: "MF_ERR_BAD_SEGMENT", 12: "MF_ERR_TOO_LARGE",
+    11: "MF_ERR_BAD_SEGMENT", 12: "MF_ERR_TOO_LARGE", 13: "MF_ERR_BAD_RANK",
 }
 
 # mf_segment: int64 x_off, int64 n, int64 y_off, int32 k, int32 pad
@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH):
             "mf_set_stream": ([vp, vp], c.c_int),
             "mf_filter": ([vp, c.c_int, vp, i64, i32, vp, vp], c.c_int),
             "mf_filter_host": ([vp, c.c_int, vp, i64, i32, vp, vp], c.c_int),
+            "mf_filter_rank": ([vp, c.c_int, vp, i64, i32, i32, vp, vp], c.c_int),
             "mf_filter_batched": ([vp, c.c_int, vp, vp, vp, i32, vp], c.c_int),
             "mf_filter_backward": ([vp, vp, vp, i64, i32, vp], c.c_int),
             "mf_filter_noalloc": ([c.c_int, vp, i64, i32, vp, vp, vp], c.c_int),
@@ -149,6 +150,14 @@ def mf_filter(handle, x, k: int, y, argmed=None):
     are contiguous CUDA tensors of the handle's device."""
     _check(load_library().mf_filter(handle, _dtype_code(x), _dptr(x, "x"), x.numel(), int(k),
                                     _dptr(y, "y"), _dptr(argmed, "argmed")), "mf_filter")
+
+
+def mf_filter_rank(handle, x, k: int, rank: int, y, argmed=None):
+    """y[i] = the element of 0-based rank `rank` in x[i .. i+k-1] (any k >= 1;
+    even k with rank = k//2 - 1 is the lower median)."""
+    _check(load_library().mf_filter_rank(handle, _dtype_code(x), _dptr(x, "x"), x.numel(),
+                                         int(k), int(rank), _dptr(y, "y"),
+                                         _dptr(argmed, "argmed")), "mf_filter_rank")
 
 
 def mf_filter_host(handle, x, k: int, y, argmed=None):

@@ -117,12 +117,31 @@ size_t batched_need(mf_handle h, const mf_segment* segs, int32_t nseg) {
     return std::max(small_need, big_need);
 }
 
-cudaError_t launch_signal(mf_handle h, const uint32_t* x, int64_t n, int k, bool is_float,
-                          uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes) {
+cudaError_t launch_signal(mf_handle h, const uint32_t* x, int64_t n, int k, int rank,
+                          bool is_float, uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes) {
     if (!use_large(h, k))
-        return mf::launch_pipeline(x, n, k, is_float, y, argmed, ws, ws_bytes, h->num_sms,
+        return mf::launch_pipeline(x, n, k, rank, is_float, y, argmed, ws, ws_bytes, h->num_sms,
                                    h->stream, &h->stats);
-    return mf::launch_large(x, n, k, is_float, y, argmed, ws, ws_bytes, h->stream, &h->stats);
+    return mf::launch_large(x, n, k, rank, is_float, y, argmed, ws, ws_bytes, h->stream,
+                            &h->stats);
+}
+
+// Shared body of mf_filter / mf_filter_rank after the window checks.
+mf_status filter_device(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32_t k,
+                        int32_t rank, void* y, int32_t* argmed) {
+    if (argmed && n > (int64_t)INT32_MAX) return MF_ERR_BAD_N;
+    if (k > h->max_k) return MF_ERR_UNSUPPORTED;
+    const size_t m = (size_t)(n - k + 1);
+    if (overlaps(x, 4 * (size_t)n, y, 4 * m)) return MF_ERR_OVERLAP;
+    if (argmed && (overlaps(x, 4 * (size_t)n, argmed, 4 * m) || overlaps(y, 4 * m, argmed, 4 * m)))
+        return MF_ERR_OVERLAP;
+    DeviceGuard g(h->device);
+    if (!g.ok) return MF_ERR_CUDA;
+    const size_t need = signal_workspace_bytes(h, n, k);
+    mf_status st = ensure_workspace(h, need);
+    if (st != MF_OK) return st;
+    return cuda_status(launch_signal(h, (const uint32_t*)x, n, k, rank, dtype == MF_FLOAT32,
+                                     (uint32_t*)y, argmed, h->ws, need));
 }
 
 }  // namespace
@@ -177,19 +196,17 @@ mf_status mf_filter(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32
                     void* y, int32_t* argmed) {
     mf_status st = check_common(h, dtype, x, n, k, y);
     if (st != MF_OK) return st;
-    if (argmed && n > (int64_t)INT32_MAX) return MF_ERR_BAD_N;
-    if (k > h->max_k) return MF_ERR_UNSUPPORTED;
-    const size_t m = (size_t)(n - k + 1);
-    if (overlaps(x, 4 * (size_t)n, y, 4 * m)) return MF_ERR_OVERLAP;
-    if (argmed && (overlaps(x, 4 * (size_t)n, argmed, 4 * m) || overlaps(y, 4 * m, argmed, 4 * m)))
-        return MF_ERR_OVERLAP;
-    DeviceGuard g(h->device);
-    if (!g.ok) return MF_ERR_CUDA;
-    const size_t need = signal_workspace_bytes(h, n, k);
-    st = ensure_workspace(h, need);
-    if (st != MF_OK) return st;
-    return cuda_status(launch_signal(h, (const uint32_t*)x, n, k, dtype == MF_FLOAT32,
-                                     (uint32_t*)y, argmed, h->ws, need));
+    return filter_device(h, dtype, x, n, k, (k - 1) / 2, y, argmed);
+}
+
+mf_status mf_filter_rank(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32_t k,
+                         int32_t rank, void* y, int32_t* argmed) {
+    if (!h || !x || !y) return MF_ERR_NULL;
+    if (dtype != MF_INT32 && dtype != MF_FLOAT32) return MF_ERR_DTYPE;
+    if (n < 1) return MF_ERR_BAD_N;
+    if (k < 1 || (int64_t)k > n) return MF_ERR_K_GT_N;
+    if (rank < 0 || rank >= k) return MF_ERR_BAD_RANK;
+    return filter_device(h, dtype, x, n, k, rank, y, argmed);
 }
 
 mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_t n, int32_t k,
@@ -213,7 +230,7 @@ mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_
     int32_t* ad = argmed_host ? (int32_t*)(base + xb + yb) : nullptr;
     cudaError_t e = cudaMemcpyAsync(xd, x_host, 4 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = launch_signal(h, xd, n, k, dtype == MF_FLOAT32, yd, ad, base + io, need);
+        e = launch_signal(h, xd, n, k, (k - 1) / 2, dtype == MF_FLOAT32, yd, ad, base + io, need);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(y_host, yd, 4 * m, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess && ad)
@@ -271,7 +288,7 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
     if (nsmall == 0) {
         for (int32_t s : big) {
             const mf_segment& d = segs[s];
-            cudaError_t e = mf::launch_large((const uint32_t*)x + d.x_off, d.n, d.k, is_float,
+            cudaError_t e = mf::launch_large((const uint32_t*)x + d.x_off, d.n, d.k, (d.k - 1) / 2, is_float,
                                              (uint32_t*)y + d.y_off, argmed ? argmed + d.y_off : nullptr,
                                              h->ws, need, h->stream, &h->stats);
             if (e != cudaSuccess) return MF_ERR_CUDA;
@@ -306,7 +323,7 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
     if (e != cudaSuccess) return MF_ERR_CUDA;
     for (int32_t s : big) {
         const mf_segment& d = segs[s];
-        e = mf::launch_large((const uint32_t*)x + d.x_off, d.n, d.k, is_float,
+        e = mf::launch_large((const uint32_t*)x + d.x_off, d.n, d.k, (d.k - 1) / 2, is_float,
                              (uint32_t*)y + d.y_off, argmed ? argmed + d.y_off : nullptr,
                              h->ws, need, h->stream, &h->stats);
         if (e != cudaSuccess) return MF_ERR_CUDA;
@@ -453,6 +470,7 @@ const char* mf_status_str(mf_status s) {
         case MF_ERR_DEVICE: return "MF_ERR_DEVICE: no such device or not compute capability 10.3";
         case MF_ERR_BAD_SEGMENT: return "MF_ERR_BAD_SEGMENT: invalid batched segment descriptor";
         case MF_ERR_TOO_LARGE: return "MF_ERR_TOO_LARGE: request exceeds the fixed no-alloc scratch";
+        case MF_ERR_BAD_RANK: return "MF_ERR_BAD_RANK: rank outside 0 .. k-1";
     }
     return "MF_ERR_UNKNOWN";
 }

@@ -130,10 +130,19 @@ inline __device__ void warp_merge_ranks(const uint32_t* kA, const uint16_t* vA, 
         if (kA[mid] <= kB[o0 - 1 - mid]) lo = mid + 1; else hi = mid;
     }
     int ia = lo, ib = o0 - lo;
+    // heads of both runs in registers (an exhausted run reads as +infinity)
+    uint64_t a = ia < NA ? kA[ia] : ~0ull;
+    uint64_t b = ib < NB ? kB[ib] : ~0ull;
     for (int o = o0; o < o1; ++o) {
-        const bool takeA = (ib >= NB) || (ia < NA && kA[ia] <= kB[ib]);
-        if (takeA) { jposA[vA[ia] - eA0] = (uint16_t)o; ++ia; }
-        else       { jposB[vB[ib] - eB0] = (uint16_t)o; ++ib; }
+        if (a <= b) {
+            jposA[vA[ia] - eA0] = (uint16_t)o;
+            ++ia;
+            a = ia < NA ? kA[ia] : ~0ull;
+        } else {
+            jposB[vB[ib] - eB0] = (uint16_t)o;
+            ++ib;
+            b = ib < NB ? kB[ib] : ~0ull;
+        }
     }
 }
 

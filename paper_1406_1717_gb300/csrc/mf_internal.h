@@ -78,7 +78,9 @@ int tune_class_of(int k);
 int pipeline_max_k();
 size_t pipeline_workspace_bytes(int64_t n, int k);
 cudaError_t pipeline_setup();
-cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, bool is_float,
+// rank: 0-based order statistic printed for every window (the median of an
+// odd window is (k - 1) / 2)
+cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, int rank, bool is_float,
                             uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes,
                             int num_sms, cudaStream_t stream, LaunchStats* stats);
 size_t pipeline_batched_workspace_bytes(const int64_t* n, const int32_t* k, int nseg);
@@ -100,7 +102,7 @@ constexpr int kLargeMaxSegs = 32;      // segments per block pair at most
 constexpr int kLargeFromK = 5001;
 size_t large_workspace_bytes(int64_t n, int k);
 cudaError_t large_setup();
-cudaError_t launch_large(const uint32_t* x, int64_t n, int k, bool is_float, uint32_t* y,
+cudaError_t launch_large(const uint32_t* x, int64_t n, int k, int rank, bool is_float, uint32_t* y,
                          int32_t* argmed, void* ws, size_t ws_bytes, cudaStream_t stream,
                          LaunchStats* stats);
 

@@ -545,11 +545,11 @@ cudaError_t large_setup()
                                 kMaxSmemBytes);
 }
 
-cudaError_t launch_large(const uint32_t* x, int64_t n, int k, bool is_float, uint32_t* y,
+cudaError_t launch_large(const uint32_t* x, int64_t n, int k, int rank, bool is_float, uint32_t* y,
                          int32_t* argmed, void* ws, size_t ws_bytes, cudaStream_t stream,
                          LaunchStats* stats)
 {
-    if (k < 1 || (k & 1) == 0 || k > kLargeMaxK || n < k) return cudaErrorInvalidValue;
+    if (k < 1 || k > kLargeMaxK || n < k || rank < 0 || rank >= k) return cudaErrorInvalidValue;
     if (ws_bytes < large_workspace_bytes(n, k)) return cudaErrorInvalidValue;
     int unw, uns, snw, sns;
     const size_t usmem = unwind_smem(k, &unw, &uns);
@@ -558,7 +558,7 @@ cudaError_t launch_large(const uint32_t* x, int64_t n, int k, bool is_float, uin
     const LargeShape sh = large_shape(n, k);
     LargeParams p{};
     p.x = x; p.y = y; p.argmed = argmed;
-    p.n = n; p.k = k; p.h = (k - 1) / 2;
+    p.n = n; p.k = k; p.h = rank;
     p.nblocks = sh.nblocks; p.npairs = sh.npairs; p.kp = sh.kp;
     p.is_float = is_float;
     p.S = sh.S; p.L = sh.L; p.LS = sh.LS;
@@ -581,7 +581,16 @@ cudaError_t launch_large(const uint32_t* x, int64_t n, int k, bool is_float, uin
         if (stats) stats->launches += 1;
         return cudaGetLastError();
     };
+    // per-call timing marks, as in the pipeline: [sort + joint ranks, unwind,
+    // segment states + chains, store]
+    cudaEvent_t* evs = nullptr;
+    if (stats && stats->timing) {
+        evs = stats->ev[stats->ring_pos % LaunchStats::kRing];
+        stats->ring_pos += 1;
+    }
+    auto mark = [&](int idx) { if (evs) cudaEventRecord(evs[idx], stream); };
     cudaError_t e;
+    mark(0);
     // phase 1: chunks, then merge tiers (ping-pong between the A and B buffers)
     const int cpb = (k + kChunk - 1) / kChunk;
     const int64_t warps = sh.nblocks * cpb;
@@ -604,18 +613,26 @@ cudaError_t launch_large(const uint32_t* x, int64_t n, int k, bool is_float, uin
         const int64_t tj = sh.npairs * 2 * sh.kp;
         large_jrank<<<(unsigned)((tj + 255) / 256), 256, 0, stream>>>(p, ks, vs);
         if ((e = launched()) != cudaSuccess) return e;
+        mark(1);
         const dim3 ug((unsigned)(sh.nblocks - 1), (unsigned)((k + kUnwindRun - 1) / kUnwindRun));
         large_unwind<<<ug, 256, usmem, stream>>>(p, vs, unw, uns);
         if ((e = launched()) != cudaSuccess) return e;
+        mark(2);
         const int64_t nseg = sh.npairs * sh.S;
         large_seginit<<<(unsigned)nseg, 256, ssmem, stream>>>(p, snw, sns);
         if ((e = launched()) != cudaSuccess) return e;
         large_chain<<<(unsigned)((nseg + 31) / 32), 32, 0, stream>>>(p);
         if ((e = launched()) != cudaSuccess) return e;
+    } else {
+        mark(1);
+        mark(2);
     }
+    mark(3);
     const int64_t m = n - k + 1;
     large_epilogue<<<(unsigned)((m + 255) / 256), 256, 0, stream>>>(p, vs);
-    return launched();
+    if ((e = launched()) != cudaSuccess) return e;
+    mark(4);
+    return cudaSuccess;
 }
 
 }  // namespace mf

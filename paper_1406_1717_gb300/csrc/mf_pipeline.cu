@@ -107,28 +107,28 @@ sortmerge_kernel(SegTable tab, SortPlan sp)
     }
     __syncthreads();
 
-    // inverse permutation (rank of each position) into valB
-    for (int e = tid; e < E; e += blockDim.x) {
-        const int blk = e / k;
-        valB[valA[e]] = (uint16_t)(e - blk * k);
+    // inverse permutation (rank of each position) into valB, block by block
+    for (int blk = 0, bstart = 0; bstart < E; ++blk, bstart += k) {
+        const int NBb = min(k, E - bstart);
+        for (int t = tid; t < NBb; t += blockDim.x)
+            valB[valA[bstart + t]] = (uint16_t)t;
     }
     __syncthreads();
 
     // per block owned by this CTA: perm, rank, sorted-order links (sentinel k)
     const int lb0 = (j0 == 1) ? 0 : 1;
-    for (int e = lb0 * k + tid; e < E; e += blockDim.x) {
-        const int blk = e / k;
-        const int pos = e - blk * k;
-        const int bstart = blk * k;
+    for (int blk = lb0, bstart = lb0 * k; bstart < E; ++blk, bstart += k) {
         const int NBb = min(k, E - bstart);
-        const int64_t gb = j0 - 1 + blk;
-        const size_t o = (size_t)gb * p.kp + pos;
-        p.perm[o] = (uint16_t)(valA[e] - bstart);                 // e = bstart + t
-        const int t = valB[e];
-        p.rnk[o] = (uint16_t)t;
-        const uint32_t pv = t > 0 ? (uint32_t)(valA[bstart + t - 1] - bstart) : (uint32_t)k;
-        const uint32_t nx = t + 1 < NBb ? (uint32_t)(valA[bstart + t + 1] - bstart) : (uint32_t)k;
-        p.slink[o] = (pv << 16) | nx;
+        const size_t ob = (size_t)(j0 - 1 + blk) * p.kp;
+        for (int pos = tid; pos < NBb; pos += blockDim.x) {
+            const int e = bstart + pos;
+            p.perm[ob + pos] = (uint16_t)(valA[e] - bstart);       // e = bstart + t
+            const int t = valB[e];
+            p.rnk[ob + pos] = (uint16_t)t;
+            const uint32_t pv = t > 0 ? (uint32_t)(valA[bstart + t - 1] - bstart) : (uint32_t)k;
+            const uint32_t nx = t + 1 < NBb ? (uint32_t)(valA[bstart + t + 1] - bstart) : (uint32_t)k;
+            p.slink[ob + pos] = (pv << 16) | nx;
+        }
     }
 
     // per pair: joint ranks by position (scratch in keyB, free after the sort)
@@ -556,23 +556,26 @@ epilogue_kernel(SegTable tab, int G)
     int32_t* as = p.argmed ? p.argmed + ebase + 1 : nullptr;
     const uint16_t* outs = p.out + (size_t)(j0 - 1) * p.kp;
     const int stride = blockDim.x;
-    // four outputs per thread per round: loads first, then lookups and stores
-    for (int o0 = threadIdx.x; o0 < nout; o0 += 4 * stride) {
-        uint32_t id[4];
-        int g[4];
+    // pair by pair (outputs g*k .. g*k + NB - 1 of this CTA); four outputs per
+    // thread per round: loads first, then lookups and stores
+    for (int g = 0, gk = 0; gk < nout; ++g, gk += k) {
+        const int cnt = min(k, nout - gk);
+        const uint16_t* og = outs + (size_t)g * p.kp;
+        for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * stride) {
+            uint32_t id[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int o = o0 + u * stride;
-            g[u] = o / k;
-            id[u] = o < nout ? (uint32_t)outs[(size_t)g[u] * p.kp + (o - g[u] * k)] : 0u;
-        }
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * stride;
+                id[u] = i < cnt ? (uint32_t)og[i] : 0u;
+            }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int o = o0 + u * stride;
-            if (o < nout) {
-                const int e = (g[u] + (int)(id[u] >> 15)) * k + (int)(id[u] & 0x7fffu);
-                ys[o] = xs[e];
-                if (as) as[o] = (int32_t)(ebase + e);
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * stride;
+                if (i < cnt) {
+                    const int e = gk + (int)(id[u] >> 15) * k + (int)(id[u] & 0x7fffu);
+                    ys[gk + i] = xs[e];
+                    if (as) as[gk + i] = (int32_t)(ebase + e);
+                }
             }
         }
     }
@@ -674,11 +677,11 @@ static void carve_signal(PipeParams& p, char*& w)
 }
 
 static void fill_signal(PipeParams& p, const uint32_t* x, uint32_t* y, int32_t* argmed,
-                        int64_t n, int k, bool is_float)
+                        int64_t n, int k, int rank, bool is_float)
 {
     p = PipeParams{};
     p.x = x; p.y = y; p.argmed = argmed;
-    p.n = n; p.k = k; p.h = (k - 1) / 2;
+    p.n = n; p.k = k; p.h = rank;
     p.nblocks = (n + k - 1) / k;
     p.npairs = p.nblocks - 1;
     p.kp = (k + 7) & ~7;
@@ -829,15 +832,16 @@ static cudaError_t launch_classes(const ClassPlan* cls, const SegTable* tabs, co
     return cudaSuccess;
 }
 
-cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, bool is_float,
+cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, int rank, bool is_float,
                             uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes,
                             int num_sms, cudaStream_t stream, LaunchStats* stats)
 {
     if (ws_bytes < pipeline_workspace_bytes(n, k)) return cudaErrorInvalidValue;
+    if (k < 1 || rank < 0 || rank >= k || n < k) return cudaErrorInvalidValue;
     SegTable tab{};
     tab.segs = nullptr;
     tab.nseg = 1;
-    fill_signal(tab.one, x, y, argmed, n, k, is_float);
+    fill_signal(tab.one, x, y, argmed, n, k, rank, is_float);
     char* w = (char*)ws;
     carve_signal(tab.one, w);
     ClassPlan cls;
@@ -906,7 +910,7 @@ cudaError_t launch_pipeline_batched(const uint32_t* x, uint32_t* y, int32_t* arg
         const int c = class_of(k[s]);
         PipeParams& p = host[fillpos[c]++];
         fill_signal(p, x + x_off[s], y + y_off[s], argmed ? argmed + y_off[s] : nullptr,
-                    n[s], k[s], is_float);
+                    n[s], k[s], (k[s] - 1) / 2, is_float);
         carve_signal(p, w);
         count_items(p, plans[cls_index[c]], tot[cls_index[c]]);
     }
