@@ -45,6 +45,12 @@ __device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
 // are all equal is skipped (common for the high bytes of smooth signals).
 // kt / vt are scratch of the same size.  On return kin / vin hold the result.
 // hist is this warp's private 256-entry counter array.
+// Adaptive step (Section 1: adaptive sorting algorithms give adaptive median
+// filters): before any pass the warp checks the adjacent pairs inside each
+// block; blocks that are all ascending keep the identity permutation and
+// need no pass, blocks that are all strictly descending are reversed.  The
+// check stops after the first 32 pairs that rule out both orders, so
+// unordered inputs pay one vote.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t sort_digit(int pass, uint32_t key, uint32_t val, int e0, int k) {
     if (pass < 4) return (key >> (8 * pass)) & 0xffu;
@@ -56,6 +62,35 @@ inline __device__ void warp_sort_group(uint32_t* kin, uint16_t* vin, uint32_t* k
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
+    {
+        bool asc = true, desc = true;
+        int pib = nblk > 1 ? lane % k : lane;          // position of pair start in its block
+        for (int base = 0; base + 1 < cnt; base += 32) {
+            const int idx = base + lane;
+            if (idx + 1 < cnt && (nblk == 1 || pib + 1 < k)) {
+                const uint32_t a = kin[idx], b = kin[idx + 1];
+                asc = asc && a <= b;
+                desc = desc && a > b;
+            }
+            if (nblk > 1) { pib += 32; while (pib >= k) pib -= k; }
+            const bool asc_out = __any_sync(kFull, !asc), desc_out = __any_sync(kFull, !desc);
+            if (asc_out && desc_out) break;             // neither order can hold
+        }
+        const bool all_asc = __all_sync(kFull, asc), all_desc = __all_sync(kFull, desc);
+        if (all_asc) { __syncwarp(); return; }
+        if (all_desc) {
+            for (int idx = lane; idx < cnt; idx += 32) {
+                const int s = (idx / k) * k, len = min(k, cnt - s);
+                const int dst = s + (len - 1 - (idx - s));
+                kt[dst] = kin[idx];
+                vt[dst] = vin[idx];
+            }
+            __syncwarp();
+            for (int idx = lane; idx < cnt; idx += 32) { kin[idx] = kt[idx]; vin[idx] = vt[idx]; }
+            __syncwarp();
+            return;
+        }
+    }
     uint32_t* ks = kin; uint16_t* vs = vin;
     uint32_t* kd = kt;  uint16_t* vd = vt;
     const int npass = nblk > 1 ? 5 : 4;

@@ -723,23 +723,34 @@ struct ClassPlan {
     int GE;       size_t ebytes;
 };
 
+// Built-in launch-plan choices per class where a measurement beat the
+// capacity rule (0 = use the rule): on GB300 at k = 1001 (n = 2^26 random
+// walk) 3 pairs per sort CTA took 2.28 ms against 2.39 ms for the largest
+// two-per-SM G = 7, and 4 pairs per store CTA 0.21 ms against 0.26 ms for 8.
+static const int kBuiltinSortG[kNumTuneClasses] = {0, 0, 3, 0, 0, 0};
+static const int kBuiltinEpiG[kNumTuneClasses] = {0, 0, 4, 0, 0, 0};
+
 static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tuning* tune,
                             ClassPlan* c)
 {
     const int W = kPipeThreads / 32;
     c->kmax = kmax;
-    // sortmerge: the largest G that keeps two CTAs per SM (one CTA if even G = 1
-    // does not), fewer when there are few pairs to spread over the SMs
-    int G = 0;
+    // sortmerge: at most the largest G that keeps two CTAs per SM (one CTA if
+    // even G = 1 does not); the class's built-in or tuned choice below that;
+    // fewer when there are few pairs to spread over the SMs
+    int Gcap = 0;
     for (int g = 1; g <= 64; ++g) {
         SortPlan t;
         size_t b;
         if (!sort_plan(kmax, g, &t, &b)) break;
-        if (b <= (size_t)kMaxSmemBytes / 2 || g == 1) G = g;
+        if (b <= (size_t)kMaxSmemBytes / 2 || g == 1) Gcap = g;
     }
-    if (G == 0) return false;
-    if (tune) tune += tune_class_of(kmax);
-    if (tune && tune->sort_G > 0 && tune->sort_G < G) G = tune->sort_G;
+    if (Gcap == 0) return false;
+    const int cls = tune_class_of(kmax);
+    if (tune) tune += cls;
+    int G = Gcap;
+    if (kBuiltinSortG[cls] > 0) G = min(G, kBuiltinSortG[cls]);
+    if (tune && tune->sort_G > 0) G = min(Gcap, tune->sort_G);
     const int64_t want = (total_pairs + 2ll * num_sms - 1) / (2ll * num_sms);
     if (want >= 1 && want < G) G = (int)want;
     sort_plan(kmax, G, &c->sp, &c->sbytes);
@@ -761,8 +772,9 @@ static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tu
     // chain
     if (!chain_plan(kmax, &c->cp, &c->cbytes)) return false;
     // epilogue
-    c->GE = max(1, min(16, 8192 / kmax));
-    if (tune && tune->epi_G > 0) c->GE = min(c->GE, tune->epi_G);
+    const int GEcap = max(1, min(16, 8192 / kmax));
+    c->GE = kBuiltinEpiG[cls] > 0 ? min(GEcap, kBuiltinEpiG[cls]) : GEcap;
+    if (tune && tune->epi_G > 0) c->GE = min(GEcap, tune->epi_G);
     c->ebytes = 4ull * (size_t)(c->GE + 1) * kmax;
     return true;
 }
