@@ -66,7 +66,10 @@ typedef enum {
     MF_ERR_BAD_RANK = 13     /* mf_filter_rank: rank outside 0 .. k-1               */
 } mf_status;
 
-typedef enum { MF_INT32 = 0, MF_FLOAT32 = 1 } mf_dtype;
+/* Element types.  Keys are compared as signed integers (int32, int64) or by
+ * IEEE 754-2008 totalOrder (float32, float64; Section 5.10 of that standard);
+ * the paper's experiments use 32-bit and 64-bit inputs (Section 6.3). */
+typedef enum { MF_INT32 = 0, MF_FLOAT32 = 1, MF_INT64 = 2, MF_FLOAT64 = 3 } mf_dtype;
 
 /* One signal of a batch.  Offsets are in elements from the x / y base
  * pointers passed to mf_filter_batched; the signal is x[x_off .. x_off+n) and
@@ -94,8 +97,9 @@ mf_status mf_set_stream(mf_handle h, void* cuda_stream);
  *  n       signal length, n >= k
  *  k       odd window size, 1 <= k <= n and k <= 262,143.  Below 5001
  *          (the handle's tier threshold, see mf_set_tier_threshold; at most
- *          9,344, one block pair in shared memory) the shared-memory
- *          pipeline runs; from it the large-k tier: global-memory merge tiers for the
+ *          9,344 for 4-byte and about 5,800 for 8-byte elements, one block
+ *          pair in shared memory) the shared-memory pipeline runs; from it
+ *          the large-k tier: global-memory merge tiers for the
  *          block sort and the post-processing chain of each block pair split
  *          into up to 32 segments, each started from a state rebuilt with the
  *          invariant of Section 5.3 (workspace about 48 + 8 * segments bytes
@@ -170,7 +174,8 @@ mf_status mf_filter_backward(mf_handle h, const float* gy, const int32_t* argmed
  * handle and allocates nothing: its scratch is a fixed 32 MiB device array
  * inside the library, present on every GPU that loads libmf.so until the
  * process exits.
- *  x, n, k, y, argmed  as mf_filter (device pointers of the current device)
+ *  x, n, k, y, argmed  as mf_filter (device pointers of the current device;
+ *                      MF_INT32 or MF_FLOAT32 only, else MF_ERR_DTYPE)
  *  cuda_stream         cudaStream_t to run on (NULL = legacy default stream)
  * Limits: the scratch a call needs is about 14 bytes per input sample
  * (8 * kp + 8 bytes per block of k samples plus 6 * kp per block pair, kp = k
@@ -204,8 +209,8 @@ mf_status mf_set_tuning(mf_handle h, int32_t k, int32_t sort_pairs_per_cta,
 /* Device workspace (bytes) that mf_filter_batched with these descriptors
  * needs on this handle (host-only computation; the request server admits
  * work by it).  Errors: MF_ERR_NULL, MF_ERR_BAD_SEGMENT. */
-mf_status mf_batched_workspace_bytes(mf_handle h, const mf_segment* segs_host, int32_t nseg,
-                                     size_t* bytes);
+mf_status mf_batched_workspace_bytes(mf_handle h, mf_dtype dtype, const mf_segment* segs_host,
+                                     int32_t nseg, size_t* bytes);
 
 /* Bytes of device workspace the handle currently holds. */
 mf_status mf_workspace_size(mf_handle h, size_t* bytes);

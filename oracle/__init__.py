@@ -31,7 +31,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-INT32, FLOAT32 = 0, 1
+INT32, FLOAT32, INT64, FLOAT64 = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -80,11 +80,11 @@ def _load():
 
 
 def _dtype_code(x: np.ndarray) -> int:
-    if x.dtype == np.int32:
-        return INT32
-    if x.dtype == np.float32:
-        return FLOAT32
-    raise TypeError(f"oracle supports int32 and float32, got {x.dtype}")
+    code = {np.dtype(np.int32): INT32, np.dtype(np.float32): FLOAT32,
+            np.dtype(np.int64): INT64, np.dtype(np.float64): FLOAT64}.get(x.dtype)
+    if code is None:
+        raise TypeError(f"oracle supports int32, float32, int64 and float64, got {x.dtype}")
+    return code
 
 
 def max_threads() -> int:

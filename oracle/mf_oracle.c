@@ -26,10 +26,11 @@
  * (Section 5.3).  Because equal keys mean equal bits, y is unique; the index
  * tie-break fixes only argmed, the index of the median element.
  *
- * Values: int32 are compared as signed integers.  float32 are compared by the
- * IEEE 754-2008 totalOrder predicate (Section 5.10 of that standard): -NaN <
- * -inf < negative numbers < -0 < +0 < positive numbers < +inf < +NaN, NaNs
- * ordered by payload.  The paper only uses integers (Section 6.2); IEEE "<"
+ * Values: int32 and int64 are compared as signed integers.  float32 and
+ * float64 are compared by the IEEE 754-2008 totalOrder predicate (Section 5.10
+ * of that standard): -NaN < -inf < negative numbers < -0 < +0 < positive
+ * numbers < +inf < +NaN, NaNs ordered by payload.  The paper's experiments
+ * use 32-bit and 64-bit inputs (Section 6.3).  The paper only uses integers (Section 6.2); IEEE "<"
  * would make -0 and +0 equal and let the result's bits depend on which of the
  * two was picked, so the oracle never uses it.
  *
@@ -50,12 +51,14 @@
 #include <omp.h>
 #endif
 
-enum { MFO_INT32 = 0, MFO_FLOAT32 = 1 };
+enum { MFO_INT32 = 0, MFO_FLOAT32 = 1, MFO_INT64 = 2, MFO_FLOAT64 = 3 };
 
 typedef struct {
-    uint32_t bits;   /* the element's raw 32 bits */
+    uint64_t bits;   /* the element's raw bits (32-bit types zero-extended) */
     int64_t index;   /* its position in x */
 } elem_t;
+
+static int elem_bytes(int dtype) { return dtype >= MFO_INT64 ? 8 : 4; }
 
 /* IEEE 754 totalOrder on binary32 bit patterns: returns <0, 0, >0. */
 static int float_total_order(uint32_t a, uint32_t b)
@@ -76,11 +79,30 @@ static int int32_order(uint32_t a, uint32_t b)
     return sa < sb ? -1 : (sa > sb ? 1 : 0);
 }
 
+/* IEEE 754 totalOrder on binary64 bit patterns, the same rule as above. */
+static int double_total_order(uint64_t a, uint64_t b)
+{
+    int neg_a = (int)(a >> 63), neg_b = (int)(b >> 63);
+    if (neg_a != neg_b)
+        return neg_a ? -1 : 1;
+    if (a == b)
+        return 0;
+    if (!neg_a)
+        return a < b ? -1 : 1;
+    return a > b ? -1 : 1;
+}
+
+static int int64_order(uint64_t a, uint64_t b)
+{
+    int64_t sa = (int64_t)a, sb = (int64_t)b;
+    return sa < sb ? -1 : (sa > sb ? 1 : 0);
+}
+
 static int cmp_int32(const void* pa, const void* pb)
 {
     const elem_t* a = (const elem_t*)pa;
     const elem_t* b = (const elem_t*)pb;
-    int c = int32_order(a->bits, b->bits);
+    int c = int32_order((uint32_t)a->bits, (uint32_t)b->bits);
     if (c) return c;
     return a->index < b->index ? -1 : (a->index > b->index ? 1 : 0);
 }
@@ -89,35 +111,67 @@ static int cmp_float32(const void* pa, const void* pb)
 {
     const elem_t* a = (const elem_t*)pa;
     const elem_t* b = (const elem_t*)pb;
-    int c = float_total_order(a->bits, b->bits);
+    int c = float_total_order((uint32_t)a->bits, (uint32_t)b->bits);
     if (c) return c;
     return a->index < b->index ? -1 : (a->index > b->index ? 1 : 0);
 }
 
+static int cmp_int64(const void* pa, const void* pb)
+{
+    const elem_t* a = (const elem_t*)pa;
+    const elem_t* b = (const elem_t*)pb;
+    int c = int64_order(a->bits, b->bits);
+    if (c) return c;
+    return a->index < b->index ? -1 : (a->index > b->index ? 1 : 0);
+}
+
+static int cmp_float64(const void* pa, const void* pb)
+{
+    const elem_t* a = (const elem_t*)pa;
+    const elem_t* b = (const elem_t*)pb;
+    int c = double_total_order(a->bits, b->bits);
+    if (c) return c;
+    return a->index < b->index ? -1 : (a->index > b->index ? 1 : 0);
+}
+
+typedef int (*cmp_fn)(const void*, const void*);
+
+static cmp_fn comparator(int dtype)
+{
+    switch (dtype) {
+        case MFO_INT32: return cmp_int32;
+        case MFO_FLOAT32: return cmp_float32;
+        case MFO_INT64: return cmp_int64;
+        default: return cmp_float64;
+    }
+}
+
 /* Element of rank r of the window that starts at x[start]; scratch holds k
  * elements. */
-static void window_select(int dtype, const uint32_t* x, int64_t start, int32_t k, int32_t r,
-                          elem_t* scratch, uint32_t* y_out, int64_t* arg_out)
+static void window_select(int dtype, const void* x, int64_t start, int32_t k, int32_t r,
+                          elem_t* scratch, void* y, int64_t yi, int64_t* arg_out)
 {
+    const int wide = elem_bytes(dtype) == 8;
     for (int32_t t = 0; t < k; ++t) {
-        scratch[t].bits = x[start + t];
+        scratch[t].bits = wide ? ((const uint64_t*)x)[start + t] : ((const uint32_t*)x)[start + t];
         scratch[t].index = start + t;
     }
-    qsort(scratch, (size_t)k, sizeof(elem_t), dtype == MFO_INT32 ? cmp_int32 : cmp_float32);
-    *y_out = scratch[r].bits;
+    qsort(scratch, (size_t)k, sizeof(elem_t), comparator(dtype));
+    if (wide) ((uint64_t*)y)[yi] = scratch[r].bits;
+    else ((uint32_t*)y)[yi] = (uint32_t)scratch[r].bits;
     if (arg_out) *arg_out = scratch[r].index;
 }
 
 /* Median (rank h of an odd window k = 2h + 1). */
-static void window_median(int dtype, const uint32_t* x, int64_t start, int32_t k,
-                          elem_t* scratch, uint32_t* y_out, int64_t* arg_out)
+static void window_median(int dtype, const void* x, int64_t start, int32_t k,
+                          elem_t* scratch, void* y, int64_t yi, int64_t* arg_out)
 {
-    window_select(dtype, x, start, k, (k - 1) / 2, scratch, y_out, arg_out);
+    window_select(dtype, x, start, k, (k - 1) / 2, scratch, y, yi, arg_out);
 }
 
 static int check_args(int dtype, const void* x, int64_t n, int32_t k)
 {
-    if (dtype != MFO_INT32 && dtype != MFO_FLOAT32) return -1;
+    if (dtype < MFO_INT32 || dtype > MFO_FLOAT64) return -1;
     if (!x || n < 1) return -2;
     if (k < 1 || (k % 2) == 0 || (int64_t)k > n) return -3;
     return 0;
@@ -127,8 +181,8 @@ static int check_args(int dtype, const void* x, int64_t n, int32_t k)
  * Full filter: y[0 .. n-k] (raw 32-bit patterns), argmed optional (may be NULL).
  * nthreads <= 0 lets OpenMP pick.  Returns 0, or a negative code on bad args.
  */
-int mfo_filter(int dtype, const uint32_t* x, int64_t n, int32_t k,
-               uint32_t* y, int64_t* argmed, int nthreads)
+int mfo_filter(int dtype, const void* x, int64_t n, int32_t k,
+               void* y, int64_t* argmed, int nthreads)
 {
     int rc = check_args(dtype, x, n, k);
     if (rc) return rc;
@@ -143,7 +197,7 @@ int mfo_filter(int dtype, const uint32_t* x, int64_t n, int32_t k,
 #pragma omp for schedule(static)
 #endif
         for (int64_t i = 0; i < m; ++i)
-            window_median(dtype, x, i, k, scratch, &y[i], argmed ? &argmed[i] : NULL);
+            window_median(dtype, x, i, k, scratch, y, i, argmed ? &argmed[i] : NULL);
         free(scratch);
     }
     return 0;
@@ -154,9 +208,9 @@ int mfo_filter(int dtype, const uint32_t* x, int64_t n, int32_t k,
  * y[j] = median of x[s .. s+k-1].  Used to check outputs of huge inputs one
  * by one.  Returns -4 if a start is out of range.
  */
-int mfo_windows(int dtype, const uint32_t* x, int64_t n, int32_t k,
+int mfo_windows(int dtype, const void* x, int64_t n, int32_t k,
                 const int64_t* starts, int64_t count,
-                uint32_t* y, int64_t* argmed, int nthreads)
+                void* y, int64_t* argmed, int nthreads)
 {
     int rc = check_args(dtype, x, n, k);
     if (rc) return rc;
@@ -172,7 +226,7 @@ int mfo_windows(int dtype, const uint32_t* x, int64_t n, int32_t k,
 #pragma omp for schedule(dynamic, 64)
 #endif
         for (int64_t j = 0; j < count; ++j)
-            window_median(dtype, x, starts[j], k, scratch, &y[j], argmed ? &argmed[j] : NULL);
+            window_median(dtype, x, starts[j], k, scratch, y, j, argmed ? &argmed[j] : NULL);
         free(scratch);
     }
     return 0;
@@ -180,7 +234,7 @@ int mfo_windows(int dtype, const uint32_t* x, int64_t n, int32_t k,
 
 static int check_rank_args(int dtype, const void* x, int64_t n, int32_t k, int32_t r)
 {
-    if (dtype != MFO_INT32 && dtype != MFO_FLOAT32) return -1;
+    if (dtype < MFO_INT32 || dtype > MFO_FLOAT64) return -1;
     if (!x || n < 1) return -2;
     if (k < 1 || (int64_t)k > n) return -3;
     if (r < 0 || r >= k) return -5;
@@ -188,8 +242,8 @@ static int check_rank_args(int dtype, const void* x, int64_t n, int32_t k, int32
 }
 
 /* Rank filter: y[i] = element of rank r in x[i .. i+k-1], i = 0 .. n-k. */
-int mfo_rank_filter(int dtype, const uint32_t* x, int64_t n, int32_t k, int32_t r,
-                    uint32_t* y, int64_t* arg, int nthreads)
+int mfo_rank_filter(int dtype, const void* x, int64_t n, int32_t k, int32_t r,
+                    void* y, int64_t* arg, int nthreads)
 {
     int rc = check_rank_args(dtype, x, n, k, r);
     if (rc) return rc;
@@ -204,15 +258,15 @@ int mfo_rank_filter(int dtype, const uint32_t* x, int64_t n, int32_t k, int32_t 
 #pragma omp for schedule(static)
 #endif
         for (int64_t i = 0; i < m; ++i)
-            window_select(dtype, x, i, k, r, scratch, &y[i], arg ? &arg[i] : NULL);
+            window_select(dtype, x, i, k, r, scratch, y, i, arg ? &arg[i] : NULL);
         free(scratch);
     }
     return 0;
 }
 
 /* Rank filter on sampled windows (see mfo_windows). */
-int mfo_rank_windows(int dtype, const uint32_t* x, int64_t n, int32_t k, int32_t r,
-                     const int64_t* starts, int64_t count, uint32_t* y, int64_t* arg,
+int mfo_rank_windows(int dtype, const void* x, int64_t n, int32_t k, int32_t r,
+                     const int64_t* starts, int64_t count, void* y, int64_t* arg,
                      int nthreads)
 {
     int rc = check_rank_args(dtype, x, n, k, r);
@@ -229,7 +283,7 @@ int mfo_rank_windows(int dtype, const uint32_t* x, int64_t n, int32_t k, int32_t
 #pragma omp for schedule(dynamic, 64)
 #endif
         for (int64_t j = 0; j < count; ++j)
-            window_select(dtype, x, starts[j], k, r, scratch, &y[j], arg ? &arg[j] : NULL);
+            window_select(dtype, x, starts[j], k, r, scratch, y, j, arg ? &arg[j] : NULL);
         free(scratch);
     }
     return 0;

@@ -25,7 +25,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmf.so")
 
-MF_INT32, MF_FLOAT32 = 0, 1
+MF_INT32, MF_FLOAT32, MF_INT64, MF_FLOAT64 = 0, 1, 2, 3
 
 STATUS_NAMES = {
     0: "MF_OK", 1: "MF_ERR_NULL", 2: "MF_ERR_BAD_N", 3: "MF_ERR_EVEN_K",
@@ -76,7 +76,7 @@ def load_library(path: str = LIB_PATH):
             "mf_set_tuning": ([vp, i32, i32, i32], c.c_int),
             "mf_set_tier_threshold": ([vp, i32], c.c_int),
             "mf_get_tier_threshold": ([vp, c.POINTER(i32)], c.c_int),
-            "mf_batched_workspace_bytes": ([vp, vp, i32, c.POINTER(sz)], c.c_int),
+            "mf_batched_workspace_bytes": ([vp, c.c_int, vp, i32, c.POINTER(sz)], c.c_int),
             "mf_workspace_size": ([vp, c.POINTER(sz)], c.c_int),
             "mf_release_workspace": ([vp], c.c_int),
             "mf_fill_splitmix": ([c.c_int, vp, i64, c.c_uint64, vp], c.c_int),
@@ -99,11 +99,11 @@ def _check(status: int, what: str):
 
 def _dtype_code(t) -> int:
     import torch
-    if t.dtype == torch.int32:
-        return MF_INT32
-    if t.dtype == torch.float32:
-        return MF_FLOAT32
-    raise TypeError(f"median filter supports int32 and float32, got {t.dtype}")
+    code = {torch.int32: MF_INT32, torch.float32: MF_FLOAT32,
+            torch.int64: MF_INT64, torch.float64: MF_FLOAT64}.get(t.dtype)
+    if code is not None:
+        return code
+    raise TypeError(f"median filter supports int32, float32, int64 and float64, got {t.dtype}")
 
 
 def _dptr(t, name: str):
@@ -171,9 +171,10 @@ def mf_filter_host(handle, x, k: int, y, argmed=None):
             return ctypes.c_void_p(a.ctypes.data)
         return _dptr(a, "host tensor")
     if isinstance(x, np.ndarray):
-        code = {np.dtype(np.int32): MF_INT32, np.dtype(np.float32): MF_FLOAT32}.get(x.dtype)
+        code = {np.dtype(np.int32): MF_INT32, np.dtype(np.float32): MF_FLOAT32,
+                np.dtype(np.int64): MF_INT64, np.dtype(np.float64): MF_FLOAT64}.get(x.dtype)
         if code is None:
-            raise TypeError(f"median filter supports int32 and float32, got {x.dtype}")
+            raise TypeError(f"median filter supports int32, float32, int64 and float64, got {x.dtype}")
         n = x.size
     else:
         code, n = _dtype_code(x), x.numel()
@@ -246,12 +247,13 @@ def tier_of(handle, k: int) -> str:
     return "large" if int(k) >= mf_get_tier_threshold(handle) else "pipeline"
 
 
-def mf_batched_workspace_bytes(handle, segs: np.ndarray) -> int:
-    """Workspace bytes mf_filter_batched needs for these descriptors on this handle."""
+def mf_batched_workspace_bytes(handle, segs: np.ndarray, dtype: int = MF_FLOAT32) -> int:
+    """Workspace bytes mf_filter_batched needs for these descriptors on this
+    handle (dtype: MF_INT32, MF_FLOAT32, MF_INT64 or MF_FLOAT64)."""
     segs = np.ascontiguousarray(segs, dtype=SEGMENT_DTYPE)
     out = ctypes.c_size_t()
-    _check(load_library().mf_batched_workspace_bytes(handle, segs.ctypes.data, len(segs),
-                                                     ctypes.byref(out)),
+    _check(load_library().mf_batched_workspace_bytes(handle, int(dtype), segs.ctypes.data,
+                                                     len(segs), ctypes.byref(out)),
            "mf_batched_workspace_bytes")
     return int(out.value)
 

@@ -52,9 +52,20 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
     return na && nb && pa < pb + nb && pb < pa + na;
 }
 
+bool dtype_ok(int dtype) {
+    return dtype == MF_INT32 || dtype == MF_FLOAT32 || dtype == MF_INT64 || dtype == MF_FLOAT64;
+}
+
+mf::Elem elem_of(int dtype) {
+    mf::Elem e;
+    e.is_float = dtype == MF_FLOAT32 || dtype == MF_FLOAT64;
+    e.wide = dtype == MF_INT64 || dtype == MF_FLOAT64;
+    return e;
+}
+
 mf_status check_common(mf_handle h, int dtype, const void* x, int64_t n, int32_t k, const void* y) {
     if (!h || !x || !y) return MF_ERR_NULL;
-    if (dtype != MF_INT32 && dtype != MF_FLOAT32) return MF_ERR_DTYPE;
+    if (!dtype_ok(dtype)) return MF_ERR_DTYPE;
     if (n < 1) return MF_ERR_BAD_N;
     if (k < 1) return MF_ERR_K_GT_N;
     if (k % 2 == 0) return MF_ERR_EVEN_K;
@@ -90,23 +101,24 @@ mf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MF_OK : MF_ERR_
 
 // Workspace of one signal: shared-memory pipeline up to pipeline_max_k(),
 // the global-memory large-k tier above it.
-bool use_large(mf_handle h, int k) {
-    return k >= h->large_from_k || k > mf::pipeline_max_k();
+bool use_large(mf_handle h, int k, bool wide) {
+    return k >= h->large_from_k || k > mf::pipeline_max_k(wide);
 }
 
-size_t signal_workspace_bytes(mf_handle h, int64_t n, int k) {
-    return use_large(h, k) ? mf::large_workspace_bytes(n, k) : mf::pipeline_workspace_bytes(n, k);
+size_t signal_workspace_bytes(mf_handle h, int64_t n, int k, bool wide) {
+    return use_large(h, k, wide) ? mf::large_workspace_bytes(n, k, wide)
+                                 : mf::pipeline_workspace_bytes(n, k);
 }
 
 // Workspace of a batched call: the pipeline group and, reusing the same
 // memory afterwards, the largest large-k signal.
-size_t batched_need(mf_handle h, const mf_segment* segs, int32_t nseg) {
+size_t batched_need(mf_handle h, const mf_segment* segs, int32_t nseg, bool wide) {
     std::vector<int64_t> nn;
     std::vector<int32_t> kk;
     size_t big_need = 0;
     for (int32_t s = 0; s < nseg; ++s) {
-        if (use_large(h, segs[s].k)) {
-            big_need = std::max(big_need, mf::large_workspace_bytes(segs[s].n, segs[s].k));
+        if (use_large(h, segs[s].k, wide)) {
+            big_need = std::max(big_need, mf::large_workspace_bytes(segs[s].n, segs[s].k, wide));
         } else {
             nn.push_back(segs[s].n);
             kk.push_back(segs[s].k);
@@ -117,13 +129,12 @@ size_t batched_need(mf_handle h, const mf_segment* segs, int32_t nseg) {
     return std::max(small_need, big_need);
 }
 
-cudaError_t launch_signal(mf_handle h, const uint32_t* x, int64_t n, int k, int rank,
-                          bool is_float, uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes) {
-    if (!use_large(h, k))
-        return mf::launch_pipeline(x, n, k, rank, is_float, y, argmed, ws, ws_bytes, h->num_sms,
+cudaError_t launch_signal(mf_handle h, const void* x, int64_t n, int k, int rank,
+                          mf::Elem el, void* y, int32_t* argmed, void* ws, size_t ws_bytes) {
+    if (!use_large(h, k, el.wide))
+        return mf::launch_pipeline(x, n, k, rank, el, y, argmed, ws, ws_bytes, h->num_sms,
                                    h->stream, &h->stats);
-    return mf::launch_large(x, n, k, rank, is_float, y, argmed, ws, ws_bytes, h->stream,
-                            &h->stats);
+    return mf::launch_large(x, n, k, rank, el, y, argmed, ws, ws_bytes, h->stream, &h->stats);
 }
 
 // Shared body of mf_filter / mf_filter_rank after the window checks.
@@ -132,16 +143,17 @@ mf_status filter_device(mf_handle h, mf_dtype dtype, const void* x, int64_t n, i
     if (argmed && n > (int64_t)INT32_MAX) return MF_ERR_BAD_N;
     if (k > h->max_k) return MF_ERR_UNSUPPORTED;
     const size_t m = (size_t)(n - k + 1);
-    if (overlaps(x, 4 * (size_t)n, y, 4 * m)) return MF_ERR_OVERLAP;
-    if (argmed && (overlaps(x, 4 * (size_t)n, argmed, 4 * m) || overlaps(y, 4 * m, argmed, 4 * m)))
+    const mf::Elem el = elem_of(dtype);
+    const size_t eb = (size_t)el.bytes();
+    if (overlaps(x, eb * (size_t)n, y, eb * m)) return MF_ERR_OVERLAP;
+    if (argmed && (overlaps(x, eb * (size_t)n, argmed, 4 * m) || overlaps(y, eb * m, argmed, 4 * m)))
         return MF_ERR_OVERLAP;
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
-    const size_t need = signal_workspace_bytes(h, n, k);
+    const size_t need = signal_workspace_bytes(h, n, k, el.wide);
     mf_status st = ensure_workspace(h, need);
     if (st != MF_OK) return st;
-    return cuda_status(launch_signal(h, (const uint32_t*)x, n, k, rank, dtype == MF_FLOAT32,
-                                     (uint32_t*)y, argmed, h->ws, need));
+    return cuda_status(launch_signal(h, x, n, k, rank, el, y, argmed, h->ws, need));
 }
 
 }  // namespace
@@ -202,7 +214,7 @@ mf_status mf_filter(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32
 mf_status mf_filter_rank(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32_t k,
                          int32_t rank, void* y, int32_t* argmed) {
     if (!h || !x || !y) return MF_ERR_NULL;
-    if (dtype != MF_INT32 && dtype != MF_FLOAT32) return MF_ERR_DTYPE;
+    if (!dtype_ok(dtype)) return MF_ERR_DTYPE;
     if (n < 1) return MF_ERR_BAD_N;
     if (k < 1 || (int64_t)k > n) return MF_ERR_K_GT_N;
     if (rank < 0 || rank >= k) return MF_ERR_BAD_RANK;
@@ -216,23 +228,26 @@ mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_
     if (argmed_host && n > (int64_t)INT32_MAX) return MF_ERR_BAD_N;
     if (k > h->max_k) return MF_ERR_UNSUPPORTED;
     const size_t m = (size_t)(n - k + 1);
-    const size_t xb = (4 * (size_t)n + 255) & ~size_t(255);
-    const size_t yb = (4 * m + 255) & ~size_t(255);
+    const mf::Elem el = elem_of(dtype);
+    const size_t eb = (size_t)el.bytes();
+    const size_t xb = (eb * (size_t)n + 255) & ~size_t(255);
+    const size_t yb = (eb * m + 255) & ~size_t(255);
+    const size_t ab = (4 * m + 255) & ~size_t(255);
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
-    const size_t io = xb + yb + (argmed_host ? yb : 0);
-    const size_t need = signal_workspace_bytes(h, n, k);
+    const size_t io = xb + yb + (argmed_host ? ab : 0);
+    const size_t need = signal_workspace_bytes(h, n, k, el.wide);
     st = ensure_workspace(h, io + need);
     if (st != MF_OK) return st;
     char* base = (char*)h->ws;
-    uint32_t* xd = (uint32_t*)base;
-    uint32_t* yd = (uint32_t*)(base + xb);
+    void* xd = base;
+    void* yd = base + xb;
     int32_t* ad = argmed_host ? (int32_t*)(base + xb + yb) : nullptr;
-    cudaError_t e = cudaMemcpyAsync(xd, x_host, 4 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+    cudaError_t e = cudaMemcpyAsync(xd, x_host, eb * (size_t)n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = launch_signal(h, xd, n, k, (k - 1) / 2, dtype == MF_FLOAT32, yd, ad, base + io, need);
+        e = launch_signal(h, xd, n, k, (k - 1) / 2, el, yd, ad, base + io, need);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(y_host, yd, 4 * m, cudaMemcpyDeviceToHost, h->stream);
+        e = cudaMemcpyAsync(y_host, yd, eb * m, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess && ad)
         e = cudaMemcpyAsync(argmed_host, ad, 4 * m, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -242,8 +257,10 @@ mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_
 mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
                             const mf_segment* segs, int32_t nseg, int32_t* argmed) {
     if (!h || !x || !y || (!segs && nseg > 0)) return MF_ERR_NULL;
-    if (dtype != MF_INT32 && dtype != MF_FLOAT32) return MF_ERR_DTYPE;
+    if (!dtype_ok(dtype)) return MF_ERR_DTYPE;
     if (nseg < 0) return MF_ERR_BAD_SEGMENT;
+    const mf::Elem el = elem_of(dtype);
+    const size_t eb = (size_t)el.bytes();
     int64_t xext = 0, yext = 0;
     std::vector<std::pair<int64_t, int64_t>> yr;
     yr.reserve((size_t)nseg);
@@ -261,9 +278,9 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
     std::sort(yr.begin(), yr.end());
     for (size_t i = 1; i < yr.size(); ++i)
         if (yr[i].first < yr[i - 1].second) return MF_ERR_OVERLAP;
-    if (overlaps(x, 4 * (size_t)xext, y, 4 * (size_t)yext)) return MF_ERR_OVERLAP;
-    if (argmed && (overlaps(x, 4 * (size_t)xext, argmed, 4 * (size_t)yext) ||
-                   overlaps(y, 4 * (size_t)yext, argmed, 4 * (size_t)yext)))
+    if (overlaps(x, eb * (size_t)xext, y, eb * (size_t)yext)) return MF_ERR_OVERLAP;
+    if (argmed && (overlaps(x, eb * (size_t)xext, argmed, 4 * (size_t)yext) ||
+                   overlaps(y, eb * (size_t)yext, argmed, 4 * (size_t)yext)))
         return MF_ERR_OVERLAP;
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
@@ -273,7 +290,7 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
     std::vector<int64_t> xo, nn, yo;
     std::vector<int32_t> kk, big;
     for (int32_t s = 0; s < nseg; ++s) {
-        if (use_large(h, segs[s].k)) {
+        if (use_large(h, segs[s].k, el.wide)) {
             big.push_back(s);
             continue;
         }
@@ -281,15 +298,14 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
         yo.push_back(segs[s].y_off); kk.push_back(segs[s].k);
     }
     const int32_t nsmall = (int32_t)kk.size();
-    const size_t need = batched_need(h, segs, nseg);
+    const size_t need = batched_need(h, segs, nseg, el.wide);
     mf_status st = ensure_workspace(h, need);
     if (st != MF_OK) return st;
-    const bool is_float = dtype == MF_FLOAT32;
     if (nsmall == 0) {
         for (int32_t s : big) {
             const mf_segment& d = segs[s];
-            cudaError_t e = mf::launch_large((const uint32_t*)x + d.x_off, d.n, d.k, (d.k - 1) / 2, is_float,
-                                             (uint32_t*)y + d.y_off, argmed ? argmed + d.y_off : nullptr,
+            cudaError_t e = mf::launch_large((const char*)x + d.x_off * eb, d.n, d.k, (d.k - 1) / 2, el,
+                                             (char*)y + d.y_off * eb, argmed ? argmed + d.y_off : nullptr,
                                              h->ws, need, h->stream, &h->stats);
             if (e != cudaSuccess) return MF_ERR_CUDA;
         }
@@ -316,15 +332,15 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
     } else if (h->stage_size < stage_need || h->stage_in_graph) {
         return MF_ERR_OOM;                            // make one uncaptured call of this size first
     }
-    cudaError_t e = mf::launch_pipeline_batched((const uint32_t*)x, (uint32_t*)y, argmed,
-                                                is_float, xo.data(), nn.data(), yo.data(),
+    cudaError_t e = mf::launch_pipeline_batched(x, y, argmed,
+                                                el, xo.data(), nn.data(), yo.data(),
                                                 kk.data(), nsmall, h->ws, need, h->stage, h->stage_size,
                                                 h->num_sms, h->stream, &h->stats);
     if (e != cudaSuccess) return MF_ERR_CUDA;
     for (int32_t s : big) {
         const mf_segment& d = segs[s];
-        e = mf::launch_large((const uint32_t*)x + d.x_off, d.n, d.k, (d.k - 1) / 2, is_float,
-                             (uint32_t*)y + d.y_off, argmed ? argmed + d.y_off : nullptr,
+        e = mf::launch_large((const char*)x + d.x_off * eb, d.n, d.k, (d.k - 1) / 2, el,
+                             (char*)y + d.y_off * eb, argmed ? argmed + d.y_off : nullptr,
                              h->ws, need, h->stream, &h->stats);
         if (e != cudaSuccess) return MF_ERR_CUDA;
     }
@@ -372,16 +388,17 @@ mf_status mf_set_tuning(mf_handle h, int32_t k, int32_t sort_pairs_per_cta, int3
     return MF_OK;
 }
 
-mf_status mf_batched_workspace_bytes(mf_handle h, const mf_segment* segs, int32_t nseg,
-                                     size_t* bytes) {
+mf_status mf_batched_workspace_bytes(mf_handle h, mf_dtype dtype, const mf_segment* segs,
+                                     int32_t nseg, size_t* bytes) {
     if (!h || !bytes || (!segs && nseg > 0)) return MF_ERR_NULL;
+    if (!dtype_ok(dtype)) return MF_ERR_DTYPE;
     if (nseg < 0) return MF_ERR_BAD_SEGMENT;
     for (int32_t s = 0; s < nseg; ++s) {
         const mf_segment& d = segs[s];
         if (d.pad != 0 || d.n < 1 || d.k < 1 || d.k % 2 == 0 || (int64_t)d.k > d.n || d.k > h->max_k)
             return MF_ERR_BAD_SEGMENT;
     }
-    *bytes = batched_need(h, segs, nseg);
+    *bytes = batched_need(h, segs, nseg, elem_of(dtype).wide);
     return MF_OK;
 }
 

@@ -28,6 +28,12 @@ __device__ __forceinline__ uint32_t from_key(uint32_t key, bool is_float) {
     if (is_float) return (key & 0x80000000u) ? (key & 0x7fffffffu) : ~key;
     return key ^ 0x80000000u;
 }
+// 64-bit elements (int64, float64): the same two maps on 64-bit patterns.
+__device__ __forceinline__ uint64_t to_key(uint64_t bits, bool is_float) {
+    const uint64_t s = 0x8000000000000000ull;
+    if (is_float) return (bits & s) ? ~bits : (bits | s);
+    return bits ^ s;
+}
 
 __device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
     for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(kFull, v, off));
@@ -52,12 +58,15 @@ __device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
 // check stops after the first 32 pairs that rule out both orders, so
 // unordered inputs pay one vote.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t sort_digit(int pass, uint32_t key, uint32_t val, int e0, int k) {
-    if (pass < 4) return (key >> (8 * pass)) & 0xffu;
+template <typename KeyT>
+__device__ __forceinline__ uint32_t sort_digit(int pass, KeyT key, uint32_t val, int e0, int k) {
+    if (pass < (int)sizeof(KeyT)) return (uint32_t)(key >> (8 * pass)) & 0xffu;
     return (val - (uint32_t)e0) / (uint32_t)k;
 }
 
-inline __device__ void warp_sort_group(uint32_t* kin, uint16_t* vin, uint32_t* kt, uint16_t* vt,
+// KeyT: uint32_t (4 key passes) or uint64_t (8 key passes).
+template <typename KeyT>
+inline __device__ void warp_sort_group(KeyT* kin, uint16_t* vin, KeyT* kt, uint16_t* vt,
                                 int cnt, int e0, int k, int nblk, uint32_t* hist)
 {
     const int lane = threadIdx.x & 31;
@@ -68,7 +77,7 @@ inline __device__ void warp_sort_group(uint32_t* kin, uint16_t* vin, uint32_t* k
         for (int base = 0; base + 1 < cnt; base += 32) {
             const int idx = base + lane;
             if (idx + 1 < cnt && (nblk == 1 || pib + 1 < k)) {
-                const uint32_t a = kin[idx], b = kin[idx + 1];
+                const KeyT a = kin[idx], b = kin[idx + 1];
                 asc = asc && a <= b;
                 desc = desc && a > b;
             }
@@ -91,14 +100,15 @@ inline __device__ void warp_sort_group(uint32_t* kin, uint16_t* vin, uint32_t* k
             return;
         }
     }
-    uint32_t* ks = kin; uint16_t* vs = vin;
-    uint32_t* kd = kt;  uint16_t* vd = vt;
-    const int npass = nblk > 1 ? 5 : 4;
+    KeyT* ks = kin; uint16_t* vs = vin;
+    KeyT* kd = kt;  uint16_t* vd = vt;
+    const int nkey = (int)sizeof(KeyT);
+    const int npass = nblk > 1 ? nkey + 1 : nkey;
     for (int pass = 0; pass < npass; ++pass) {
         for (int d = lane; d < 256; d += 32) hist[d] = 0;
         __syncwarp();
         for (int idx = lane; idx < cnt; idx += 32)
-            atomicAdd(&hist[sort_digit(pass, ks[idx], vs[idx], e0, k)], 1u);
+            atomicAdd(&hist[sort_digit<KeyT>(pass, ks[idx], vs[idx], e0, k)], 1u);
         __syncwarp();
         // exclusive scan of the 256 counters: lane owns entries 8*lane .. 8*lane+7
         uint32_t c[8], s = 0, mx = 0;
@@ -119,8 +129,9 @@ inline __device__ void warp_sort_group(uint32_t* kin, uint16_t* vin, uint32_t* k
         for (int base = 0; base < cnt; base += 32) {
             const int idx = base + lane;
             const bool valid = idx < cnt;
-            uint32_t key = 0, val = 0, d = 0x100u + (uint32_t)lane;   // unique for idle lanes
-            if (valid) { key = ks[idx]; val = vs[idx]; d = sort_digit(pass, key, val, e0, k); }
+            KeyT key = 0;
+            uint32_t val = 0, d = 0x100u + (uint32_t)lane;           // unique for idle lanes
+            if (valid) { key = ks[idx]; val = vs[idx]; d = sort_digit<KeyT>(pass, key, val, e0, k); }
             const uint32_t peers = __match_any_sync(kFull, d);
             const int leader = __ffs(peers) - 1;
             uint32_t b = 0;
@@ -133,7 +144,7 @@ inline __device__ void warp_sort_group(uint32_t* kin, uint16_t* vin, uint32_t* k
             }
             __syncwarp();
         }
-        uint32_t* tk = ks; ks = kd; kd = tk;
+        KeyT* tk = ks; ks = kd; kd = tk;
         uint16_t* tv = vs; vs = vd; vd = tv;
     }
     if (ks != kin) {
@@ -150,8 +161,9 @@ inline __device__ void warp_sort_group(uint32_t* kin, uint16_t* vin, uint32_t* k
 // Warp-cooperative merge path: lane L emits merged positions
 // [L*per, (L+1)*per).  Results are stored by position (jposA / jposB).
 // ---------------------------------------------------------------------------
-inline __device__ void warp_merge_ranks(const uint32_t* kA, const uint16_t* vA, int NA, int eA0,
-                                 const uint32_t* kB, const uint16_t* vB, int NB, int eB0,
+template <typename KeyT>
+inline __device__ void warp_merge_ranks(const KeyT* kA, const uint16_t* vA, int NA, int eA0,
+                                 const KeyT* kB, const uint16_t* vB, int NB, int eB0,
                                  uint16_t* jposA, uint16_t* jposB)
 {
     const int lane = threadIdx.x & 31;
@@ -165,18 +177,18 @@ inline __device__ void warp_merge_ranks(const uint32_t* kA, const uint16_t* vA, 
         if (kA[mid] <= kB[o0 - 1 - mid]) lo = mid + 1; else hi = mid;
     }
     int ia = lo, ib = o0 - lo;
-    // heads of both runs in registers (an exhausted run reads as +infinity)
-    uint64_t a = ia < NA ? kA[ia] : ~0ull;
-    uint64_t b = ib < NB ? kB[ib] : ~0ull;
+    // heads of both runs in registers
+    KeyT a = ia < NA ? kA[ia] : KeyT(0);
+    KeyT b = ib < NB ? kB[ib] : KeyT(0);
     for (int o = o0; o < o1; ++o) {
-        if (a <= b) {
+        if (ib >= NB || (ia < NA && a <= b)) {
             jposA[vA[ia] - eA0] = (uint16_t)o;
             ++ia;
-            a = ia < NA ? kA[ia] : ~0ull;
+            if (ia < NA) a = kA[ia];
         } else {
             jposB[vB[ib] - eB0] = (uint16_t)o;
             ++ib;
-            b = ib < NB ? kB[ib] : ~0ull;
+            if (ib < NB) b = kB[ib];
         }
     }
 }

@@ -12,8 +12,8 @@ constexpr int kMaxSmemBytes = 227 * 1024;          // opt-in dynamic shared memo
 constexpr int kPipeThreads = 256;
 
 struct PipeParams {
-    const uint32_t* x;
-    uint32_t* y;
+    const void* x;            // n elements of 4 bytes (int32, float32) or 8 (int64, float64)
+    void* y;
     int32_t* argmed;
     int64_t n, nblocks, npairs;
     int k, h, kp;             // kp: k rounded up to a multiple of 8 (16-byte rows)
@@ -75,18 +75,25 @@ struct LaunchStats {
 constexpr int kNumTuneClasses = 6;     // classes of k: <= 64, 256, 1021, 2047, 4095, larger
 int tune_class_of(int k);
 
-int pipeline_max_k();
+// Element type of a call: float or integer, 4 or 8 bytes.
+struct Elem {
+    bool is_float;
+    bool wide;                // 8-byte elements
+    int bytes() const { return wide ? 8 : 4; }
+};
+
+int pipeline_max_k(bool wide = false);
 size_t pipeline_workspace_bytes(int64_t n, int k);
 cudaError_t pipeline_setup();
 // rank: 0-based order statistic printed for every window (the median of an
 // odd window is (k - 1) / 2)
-cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, int rank, bool is_float,
-                            uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes,
+cudaError_t launch_pipeline(const void* x, int64_t n, int k, int rank, Elem el,
+                            void* y, int32_t* argmed, void* ws, size_t ws_bytes,
                             int num_sms, cudaStream_t stream, LaunchStats* stats);
 size_t pipeline_batched_workspace_bytes(const int64_t* n, const int32_t* k, int nseg);
 // Batched: `stage` is host memory (pinned for graph capture) of at least
 // nseg * sizeof(PipeParams) bytes that must stay unchanged until the copy ran.
-cudaError_t launch_pipeline_batched(const uint32_t* x, uint32_t* y, int32_t* argmed, bool is_float,
+cudaError_t launch_pipeline_batched(const void* x, void* y, int32_t* argmed, Elem el,
                                     const int64_t* x_off, const int64_t* n, const int64_t* y_off,
                                     const int32_t* k, int nseg, void* ws, size_t ws_bytes,
                                     void* stage, size_t stage_bytes, int num_sms,
@@ -100,9 +107,9 @@ constexpr int kLargeMaxSegs = 32;      // segments per block pair at most
 // float32) the large-k tier is faster than the shared-memory pipeline from
 // k of about 5000 (4095: 4.4 vs 5.6 ms; 6001: 7.2 vs 5.9 ms).
 constexpr int kLargeFromK = 5001;
-size_t large_workspace_bytes(int64_t n, int k);
 cudaError_t large_setup();
-cudaError_t launch_large(const uint32_t* x, int64_t n, int k, int rank, bool is_float, uint32_t* y,
+size_t large_workspace_bytes(int64_t n, int k, bool wide);
+cudaError_t launch_large(const void* x, int64_t n, int k, int rank, Elem el, void* y,
                          int32_t* argmed, void* ws, size_t ws_bytes, cudaStream_t stream,
                          LaunchStats* stats);
 

@@ -43,8 +43,8 @@ constexpr uint32_t kBFlag = 0x80000000u;          // node id of B's element
 constexpr uint32_t kInf = 0xffffffffu;           // joint rank of the sentinels
 
 struct LargeParams {
-    const uint32_t* x;
-    uint32_t* y;
+    const void* x;                               // 4- or 8-byte elements
+    void* y;
     int32_t* argmed;
     int64_t n, nblocks, npairs;
     int k, h;
@@ -52,7 +52,8 @@ struct LargeParams {
     bool is_float;
     int S, L;                                    // segments per pair, steps per segment
     int64_t LS;                                  // list stride: k + 2 rounded up to 32
-    uint32_t *keyA, *valA, *keyB, *valB;         // [nblocks][kp] sort ping-pong
+    void *keyA, *keyB;                           // [nblocks][kp] sort keys (4 or 8 bytes)
+    uint32_t *valA, *valB;                       // [nblocks][kp] positions (ping-pong)
     uint32_t* rnk;                               // [nblocks][kp] rank of position p
     uint2* ulink;                                // [nblocks][kp] unwind (prev, next), sentinel k+1
     uint32_t* ja;                                // [npairs][kp] joint rank of A's position p
@@ -117,8 +118,10 @@ __device__ __forceinline__ int bits_last_before(const uint32_t* W, const uint32_
 }
 
 // ---------------------------------------------------------------------------
-constexpr size_t kChunkWarpBytes = (size_t)kChunk * 12 + 1024;
+template <typename KeyT>
+__host__ __device__ constexpr size_t chunk_warp_bytes() { return (size_t)kChunk * (2 * sizeof(KeyT) + 4) + 1024; }
 
+template <typename KeyT>
 __global__ void __launch_bounds__(256)
 large_chunk_sort(LargeParams p, int chunks_per_block)
 {
@@ -132,25 +135,27 @@ large_chunk_sort(LargeParams p, int chunks_per_block)
     const int lo = c * kChunk;
     const int cnt = min(kChunk, NB - lo);
     if (cnt <= 0) return;
-    unsigned char* ws = smem + (size_t)warp * kChunkWarpBytes;
-    uint32_t* ka = reinterpret_cast<uint32_t*>(ws);
-    uint32_t* kb = ka + kChunk;
+    unsigned char* ws = smem + (size_t)warp * chunk_warp_bytes<KeyT>();
+    KeyT* ka = reinterpret_cast<KeyT*>(ws);
+    KeyT* kb = ka + kChunk;
     uint16_t* va = reinterpret_cast<uint16_t*>(kb + kChunk);
     uint16_t* vb = va + kChunk;
     uint32_t* hist = reinterpret_cast<uint32_t*>(vb + kChunk);
-    const uint32_t* xs = p.x + b * (int64_t)p.k + lo;
+    const KeyT* xs = reinterpret_cast<const KeyT*>(p.x) + b * (int64_t)p.k + lo;
     for (int t = lane; t < cnt; t += 32) { ka[t] = to_key(__ldg(xs + t), p.is_float); va[t] = (uint16_t)t; }
     __syncwarp();
-    warp_sort_group(ka, va, kb, vb, cnt, 0, kChunk, 1, hist);
+    warp_sort_group<KeyT>(ka, va, kb, vb, cnt, 0, kChunk, 1, hist);
     const int64_t o = b * p.kp + lo;
-    for (int t = lane; t < cnt; t += 32) { p.keyA[o + t] = ka[t]; p.valA[o + t] = (uint32_t)lo + va[t]; }
+    KeyT* keys = reinterpret_cast<KeyT*>(p.keyA);
+    for (int t = lane; t < cnt; t += 32) { keys[o + t] = ka[t]; p.valA[o + t] = (uint32_t)lo + va[t]; }
 }
 
 // sorted runs [l0, l0+R) and [l0+R, l0+2R) of every block -> one run; each
 // thread writes 4 consecutive outputs after a merge-path search
+template <typename KeyT>
 __global__ void __launch_bounds__(256)
-large_merge(LargeParams p, const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int R, int per_block)
+large_merge(LargeParams p, const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
+            KeyT* __restrict__ kout, uint32_t* __restrict__ vout, int R, int per_block)
 {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t b = gid / per_block;
@@ -162,8 +167,8 @@ large_merge(LargeParams p, const uint32_t* __restrict__ kin, const uint32_t* __r
     const int l0 = (o / (2 * R)) * 2 * R, r0 = min(l0 + R, NB);
     const int lenL = r0 - l0, lenR = min(l0 + 2 * R, NB) - r0;
     const int d = o - l0;
-    const uint32_t* KL = kin + base + l0;
-    const uint32_t* KR = kin + base + r0;
+    const KeyT* KL = kin + base + l0;
+    const KeyT* KR = kin + base + r0;
     int lo = max(0, d - lenR), hi = min(d, lenL);
     while (lo < hi) {                              // ia = #left elements among the first d
         const int mid = (lo + hi) >> 1;
@@ -191,8 +196,9 @@ large_ranks(LargeParams p, const uint32_t* __restrict__ vs)
 
 // joint rank of every element of pair q (A = block q, B = block q+1):
 // A's t-th smallest -> t + #{B keys < key}; B's u-th -> u + #{A keys <= key}
+template <typename KeyT>
 __global__ void __launch_bounds__(256)
-large_jrank(LargeParams p, const uint32_t* __restrict__ ks, const uint32_t* __restrict__ vs)
+large_jrank(LargeParams p, const KeyT* __restrict__ ks, const uint32_t* __restrict__ vs)
 {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t per_pair = 2 * p.kp;
@@ -203,7 +209,7 @@ large_jrank(LargeParams p, const uint32_t* __restrict__ ks, const uint32_t* __re
     const int64_t abase = q * p.kp, bbase = (q + 1) * p.kp;
     uint32_t* M = p.M + q * per_pair;
     if (e < NA) {
-        const uint32_t key = ks[abase + e];
+        const KeyT key = ks[abase + e];
         int lo = 0, hi = NB;
         while (lo < hi) { const int mid = (lo + hi) >> 1; if (ks[bbase + mid] < key) lo = mid + 1; else hi = mid; }
         const uint32_t pos = vs[abase + e];
@@ -211,7 +217,7 @@ large_jrank(LargeParams p, const uint32_t* __restrict__ ks, const uint32_t* __re
         p.ja[q * p.kp + pos] = (uint32_t)(e + lo);
     } else if (e >= (int)p.kp && e - (int)p.kp < NB) {
         const int u = e - (int)p.kp;
-        const uint32_t key = ks[bbase + u];
+        const KeyT key = ks[bbase + u];
         int lo = 0, hi = NA;
         while (lo < hi) { const int mid = (lo + hi) >> 1; if (ks[abase + mid] <= key) lo = mid + 1; else hi = mid; }
         const uint32_t pos = vs[bbase + u];
@@ -466,6 +472,7 @@ large_chain(LargeParams p)
     }
 }
 
+template <typename ValT>
 __global__ void __launch_bounds__(256)
 large_epilogue(LargeParams p, const uint32_t* __restrict__ vs)
 {
@@ -480,7 +487,7 @@ large_epilogue(LargeParams p, const uint32_t* __restrict__ vs)
         const uint32_t id = p.out[q * p.kp + i];
         src = (q + (id >> 31)) * (int64_t)p.k + (id & ~kBFlag);
     }
-    p.y[o] = __ldg(p.x + src);
+    reinterpret_cast<ValT*>(p.y)[o] = __ldg(reinterpret_cast<const ValT*>(p.x) + src);
     if (p.argmed) p.argmed[o] = (int32_t)src;
 }
 
@@ -520,12 +527,14 @@ static size_t seginit_smem(int k, int* nw, int* ns)
     return 8ull * (size_t)(*nw + *ns) + 2 * 4 * 256 + 16;
 }
 
-size_t large_workspace_bytes(int64_t n, int k)
+size_t large_workspace_bytes(int64_t n, int k, bool wide)
 {
     const LargeShape s = large_shape(n, k);
     const uint64_t nb = (uint64_t)s.nblocks, kp = (uint64_t)s.kp;
     const uint64_t np1 = (uint64_t)(s.npairs > 0 ? s.npairs : 1);
-    uint64_t b = a256(4ull * nb * kp) * 5;                   // keyA valA keyB valB rnk
+    const uint64_t kb = wide ? 8 : 4;
+    uint64_t b = a256(kb * nb * kp) * 2;                     // keyA keyB
+    b += a256(4ull * nb * kp) * 3;                           // valA valB rnk
     b += a256(8ull * nb * kp);                               // ulink
     b += a256(4ull * np1 * kp) * 3;                          // ja jb out
     b += a256(8ull * np1 * kp);                              // M
@@ -537,46 +546,24 @@ size_t large_workspace_bytes(int64_t n, int k)
 cudaError_t large_setup()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(large_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(8 * kChunkWarpBytes)))) return e;
+    if ((e = cudaFuncSetAttribute(large_chunk_sort<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(8 * chunk_warp_bytes<uint32_t>())))) return e;
+    if ((e = cudaFuncSetAttribute(large_chunk_sort<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(8 * chunk_warp_bytes<uint64_t>())))) return e;
     if ((e = cudaFuncSetAttribute(large_unwind, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kMaxSmemBytes))) return e;
     return cudaFuncSetAttribute(large_seginit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kMaxSmemBytes);
 }
 
-cudaError_t launch_large(const uint32_t* x, int64_t n, int k, int rank, bool is_float, uint32_t* y,
-                         int32_t* argmed, void* ws, size_t ws_bytes, cudaStream_t stream,
-                         LaunchStats* stats)
+// All launches of one call; KeyT = uint32_t or uint64_t (key and element width).
+template <typename KeyT>
+static cudaError_t run_large(LargeParams& p, const LargeShape& sh, size_t usmem, int unw, int uns,
+                             size_t ssmem, int snw, int sns, cudaStream_t stream,
+                             LaunchStats* stats)
 {
-    if (k < 1 || k > kLargeMaxK || n < k || rank < 0 || rank >= k) return cudaErrorInvalidValue;
-    if (ws_bytes < large_workspace_bytes(n, k)) return cudaErrorInvalidValue;
-    int unw, uns, snw, sns;
-    const size_t usmem = unwind_smem(k, &unw, &uns);
-    const size_t ssmem = seginit_smem(k, &snw, &sns);
-    if (usmem > (size_t)kMaxSmemBytes || ssmem > (size_t)kMaxSmemBytes) return cudaErrorInvalidValue;
-    const LargeShape sh = large_shape(n, k);
-    LargeParams p{};
-    p.x = x; p.y = y; p.argmed = argmed;
-    p.n = n; p.k = k; p.h = rank;
-    p.nblocks = sh.nblocks; p.npairs = sh.npairs; p.kp = sh.kp;
-    p.is_float = is_float;
-    p.S = sh.S; p.L = sh.L; p.LS = sh.LS;
-    const uint64_t nb = (uint64_t)sh.nblocks, kp = (uint64_t)sh.kp;
-    const uint64_t np1 = (uint64_t)(sh.npairs > 0 ? sh.npairs : 1);
-    char* w = (char*)ws;
-    p.keyA = (uint32_t*)w; w += a256(4ull * nb * kp);
-    p.valA = (uint32_t*)w; w += a256(4ull * nb * kp);
-    p.keyB = (uint32_t*)w; w += a256(4ull * nb * kp);
-    p.valB = (uint32_t*)w; w += a256(4ull * nb * kp);
-    p.rnk = (uint32_t*)w;  w += a256(4ull * nb * kp);
-    p.ulink = (uint2*)w;   w += a256(8ull * nb * kp);
-    p.ja = (uint32_t*)w;   w += a256(4ull * np1 * kp);
-    p.jb = (uint32_t*)w;   w += a256(4ull * np1 * kp);
-    p.out = (uint32_t*)w;  w += a256(4ull * np1 * kp);
-    p.M = (uint32_t*)w;    w += a256(8ull * np1 * kp);
-    p.seg = (int4*)w;      w += a256(16ull * np1 * sh.S);
-    p.lists = (uint2*)w;
+    const int k = p.k;
+    const uint64_t kp = (uint64_t)sh.kp;
     auto launched = [&]() -> cudaError_t {
         if (stats) stats->launches += 1;
         return cudaGetLastError();
@@ -594,15 +581,16 @@ cudaError_t launch_large(const uint32_t* x, int64_t n, int k, int rank, bool is_
     // phase 1: chunks, then merge tiers (ping-pong between the A and B buffers)
     const int cpb = (k + kChunk - 1) / kChunk;
     const int64_t warps = sh.nblocks * cpb;
-    large_chunk_sort<<<(unsigned)((warps + 7) / 8), 256, 8 * kChunkWarpBytes, stream>>>(p, cpb);
+    large_chunk_sort<KeyT><<<(unsigned)((warps + 7) / 8), 256, 8 * chunk_warp_bytes<KeyT>(), stream>>>(p, cpb);
     if ((e = launched()) != cudaSuccess) return e;
-    uint32_t *ks = p.keyA, *vs = p.valA, *kt = p.keyB, *vt = p.valB;
+    KeyT *ks = (KeyT*)p.keyA, *kt = (KeyT*)p.keyB;
+    uint32_t *vs = p.valA, *vt = p.valB;
     const int per_block4 = (int)(kp / 4);
     for (int R = kChunk; R < k; R *= 2) {
         const int64_t threads = sh.nblocks * per_block4;
-        large_merge<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(p, ks, vs, kt, vt, R, per_block4);
+        large_merge<KeyT><<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(p, ks, vs, kt, vt, R, per_block4);
         if ((e = launched()) != cudaSuccess) return e;
-        uint32_t* t1 = ks; ks = kt; kt = t1;
+        KeyT* t1 = ks; ks = kt; kt = t1;
         uint32_t* t2 = vs; vs = vt; vt = t2;
     }
     if (sh.npairs > 0) {
@@ -611,7 +599,7 @@ cudaError_t launch_large(const uint32_t* x, int64_t n, int k, int rank, bool is_
         large_ranks<<<(unsigned)((tr + 255) / 256), 256, 0, stream>>>(p, vs);
         if ((e = launched()) != cudaSuccess) return e;
         const int64_t tj = sh.npairs * 2 * sh.kp;
-        large_jrank<<<(unsigned)((tj + 255) / 256), 256, 0, stream>>>(p, ks, vs);
+        large_jrank<KeyT><<<(unsigned)((tj + 255) / 256), 256, 0, stream>>>(p, ks, vs);
         if ((e = launched()) != cudaSuccess) return e;
         mark(1);
         const dim3 ug((unsigned)(sh.nblocks - 1), (unsigned)((k + kUnwindRun - 1) / kUnwindRun));
@@ -628,11 +616,48 @@ cudaError_t launch_large(const uint32_t* x, int64_t n, int k, int rank, bool is_
         mark(2);
     }
     mark(3);
-    const int64_t m = n - k + 1;
-    large_epilogue<<<(unsigned)((m + 255) / 256), 256, 0, stream>>>(p, vs);
+    const int64_t m = p.n - k + 1;
+    large_epilogue<KeyT><<<(unsigned)((m + 255) / 256), 256, 0, stream>>>(p, vs);
     if ((e = launched()) != cudaSuccess) return e;
     mark(4);
     return cudaSuccess;
+}
+
+cudaError_t launch_large(const void* x, int64_t n, int k, int rank, Elem el, void* y,
+                         int32_t* argmed, void* ws, size_t ws_bytes, cudaStream_t stream,
+                         LaunchStats* stats)
+{
+    if (k < 1 || k > kLargeMaxK || n < k || rank < 0 || rank >= k) return cudaErrorInvalidValue;
+    if (ws_bytes < large_workspace_bytes(n, k, el.wide)) return cudaErrorInvalidValue;
+    int unw, uns, snw, sns;
+    const size_t usmem = unwind_smem(k, &unw, &uns);
+    const size_t ssmem = seginit_smem(k, &snw, &sns);
+    if (usmem > (size_t)kMaxSmemBytes || ssmem > (size_t)kMaxSmemBytes) return cudaErrorInvalidValue;
+    const LargeShape sh = large_shape(n, k);
+    LargeParams p{};
+    p.x = x; p.y = y; p.argmed = argmed;
+    p.n = n; p.k = k; p.h = rank;
+    p.nblocks = sh.nblocks; p.npairs = sh.npairs; p.kp = sh.kp;
+    p.is_float = el.is_float;
+    p.S = sh.S; p.L = sh.L; p.LS = sh.LS;
+    const uint64_t nb = (uint64_t)sh.nblocks, kp = (uint64_t)sh.kp;
+    const uint64_t np1 = (uint64_t)(sh.npairs > 0 ? sh.npairs : 1);
+    const uint64_t kb = (uint64_t)el.bytes();
+    char* w = (char*)ws;
+    p.keyA = w;            w += a256(kb * nb * kp);
+    p.keyB = w;            w += a256(kb * nb * kp);
+    p.valA = (uint32_t*)w; w += a256(4ull * nb * kp);
+    p.valB = (uint32_t*)w; w += a256(4ull * nb * kp);
+    p.rnk = (uint32_t*)w;  w += a256(4ull * nb * kp);
+    p.ulink = (uint2*)w;   w += a256(8ull * nb * kp);
+    p.ja = (uint32_t*)w;   w += a256(4ull * np1 * kp);
+    p.jb = (uint32_t*)w;   w += a256(4ull * np1 * kp);
+    p.out = (uint32_t*)w;  w += a256(4ull * np1 * kp);
+    p.M = (uint32_t*)w;    w += a256(8ull * np1 * kp);
+    p.seg = (int4*)w;      w += a256(16ull * np1 * sh.S);
+    p.lists = (uint2*)w;
+    if (el.wide) return run_large<uint64_t>(p, sh, usmem, unw, uns, ssmem, snw, sns, stream, stats);
+    return run_large<uint32_t>(p, sh, usmem, unw, uns, ssmem, snw, sns, stream, stats);
 }
 
 }  // namespace mf

@@ -90,8 +90,10 @@ extern "C" mf_status mf_filter_noalloc(mf_dtype dtype, const void* x, int64_t n,
     if (st != MF_OK) return st;
     // Every element of the scratch that the kernels read is written earlier in
     // the same call, so nothing has to be cleared between calls.
-    const cudaError_t e = mf::launch_pipeline((const uint32_t*)x, n, k, (k - 1) / 2, dtype == MF_FLOAT32,
-                                              (uint32_t*)y, argmed, slot->scratch,
+    mf::Elem el;
+    el.is_float = dtype == MF_FLOAT32;
+    el.wide = false;
+    const cudaError_t e = mf::launch_pipeline(x, n, k, (k - 1) / 2, el, y, argmed, slot->scratch,
                                               kNoAllocScratchBytes, slot->num_sms,
                                               (cudaStream_t)cuda_stream, nullptr);
     return e == cudaSuccess ? MF_OK : MF_ERR_CUDA;

@@ -63,14 +63,17 @@ __device__ __forceinline__ PipeParams find_signal(const SegTable& t, int kern, i
 // ===========================================================================
 // sortmerge_kernel
 // ===========================================================================
+// KeyT: uint32_t for 4-byte elements, uint64_t for 8-byte elements.
+template <typename KeyT>
 __global__ void __launch_bounds__(kPipeThreads)
 sortmerge_kernel(SegTable tab, SortPlan sp)
 {
     int64_t cta;
     const PipeParams p = find_signal(tab, kItemSort, blockIdx.x, &cta);
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* keyA = reinterpret_cast<uint32_t*>(smem + sp.off_keyA);
-    uint32_t* keyB = reinterpret_cast<uint32_t*>(smem + sp.off_keyB);
+    KeyT* keyA = reinterpret_cast<KeyT*>(smem + sp.off_keyA);
+    KeyT* keyB = reinterpret_cast<KeyT*>(smem + sp.off_keyB);
+    const KeyT* xp = reinterpret_cast<const KeyT*>(p.x);
     uint16_t* valA = reinterpret_cast<uint16_t*>(smem + sp.off_valA);
     uint16_t* valB = reinterpret_cast<uint16_t*>(smem + sp.off_valB);
     uint32_t* hist = reinterpret_cast<uint32_t*>(smem + sp.off_hist);
@@ -91,7 +94,7 @@ sortmerge_kernel(SegTable tab, SortPlan sp)
     bpg = max(1, min(bpg, cap));
 
     for (int e = tid; e < E; e += blockDim.x) {
-        keyA[e] = to_key(__ldg(p.x + ebase + e), p.is_float);
+        keyA[e] = to_key(__ldg(xp + ebase + e), p.is_float);
         valA[e] = (uint16_t)e;
     }
     __syncthreads();
@@ -102,7 +105,7 @@ sortmerge_kernel(SegTable tab, SortPlan sp)
         const int b1 = min(b0 + bpg, nblk);
         const int e0 = b0 * k;
         const int e1 = min(b1 * k, E);
-        warp_sort_group(keyA + e0, valA + e0, keyB + e0, valB + e0,
+        warp_sort_group<KeyT>(keyA + e0, valA + e0, keyB + e0, valB + e0,
                         max(0, e1 - e0), e0, k, b1 - b0, hist + warp * 256);
     }
     __syncthreads();
@@ -135,7 +138,7 @@ sortmerge_kernel(SegTable tab, SortPlan sp)
     uint16_t* jp = reinterpret_cast<uint16_t*>(keyB);
     for (int g = warp; g < npair; g += W) {
         const int NB = min(k, E - (g + 1) * k);
-        warp_merge_ranks(keyA + g * k, valA + g * k, k, g * k,
+        warp_merge_ranks<KeyT>(keyA + g * k, valA + g * k, k, g * k,
                          keyA + (g + 1) * k, valA + (g + 1) * k, NB, (g + 1) * k,
                          jp + (size_t)g * 2 * k, jp + (size_t)g * 2 * k + k);
     }
@@ -535,11 +538,12 @@ chain_kernel(SegTable tab, ChainPlan cp)
 // epilogue_kernel: y[(j-1)k + 1 + i] = the element printed at step i of pair
 // j, read from a shared-memory copy of the CTA's input span; y[0] = X_0[P_0[h]].
 // ===========================================================================
+template <typename ValT>
 __global__ void __launch_bounds__(kPipeThreads)
 epilogue_kernel(SegTable tab, int G)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* xs = reinterpret_cast<uint32_t*>(smem);
+    ValT* xs = reinterpret_cast<ValT*>(smem);
     int64_t cta;
     const PipeParams p = find_signal(tab, kItemEpilogue, blockIdx.x, &cta);
     const int k = p.k;
@@ -549,10 +553,11 @@ epilogue_kernel(SegTable tab, int G)
     const int64_t ebase = (j0 - 1) * (int64_t)k;
     const int64_t rem = p.n - ebase;
     const int E = (int)((int64_t)(npair + 1) * k < rem ? (int64_t)(npair + 1) * k : rem);
-    for (int e = threadIdx.x; e < E; e += blockDim.x) xs[e] = __ldg(p.x + ebase + e);
+    const ValT* xp = reinterpret_cast<const ValT*>(p.x);
+    for (int e = threadIdx.x; e < E; e += blockDim.x) xs[e] = __ldg(xp + ebase + e);
     __syncthreads();
     const int nout = npair > 0 ? E - k : 0;
-    uint32_t* ys = p.y + ebase + 1;
+    ValT* ys = reinterpret_cast<ValT*>(p.y) + ebase + 1;
     int32_t* as = p.argmed ? p.argmed + ebase + 1 : nullptr;
     const uint16_t* outs = p.out + (size_t)(j0 - 1) * p.kp;
     const int stride = blockDim.x;
@@ -581,7 +586,7 @@ epilogue_kernel(SegTable tab, int G)
     }
     if (j0 == 1 && threadIdx.x == 0) {
         const int pm = p.perm[p.h];
-        p.y[0] = xs[pm];
+        reinterpret_cast<ValT*>(p.y)[0] = xs[pm];
         if (p.argmed) p.argmed[0] = pm;
     }
 }
@@ -592,14 +597,15 @@ epilogue_kernel(SegTable tab, int G)
 static inline uint64_t al16(uint64_t v) { return (v + 15) & ~uint64_t(15); }
 static inline uint64_t al256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
 
-static bool sort_plan(int k, int G, SortPlan* sp, size_t* bytes)
+static bool sort_plan(int k, int G, SortPlan* sp, size_t* bytes, bool wide)
 {
     const int W = kPipeThreads / 32;
     const uint64_t E = (uint64_t)(G + 1) * k;
+    const uint64_t kb = wide ? 8 : 4;
     if (E > 65535) return false;
     uint64_t off = 0;
-    sp->off_keyA = (uint32_t)off; off = al16(off + 4 * E);
-    sp->off_keyB = (uint32_t)off; off = al16(off + 4 * E);
+    sp->off_keyA = (uint32_t)off; off = al16(off + kb * E);
+    sp->off_keyB = (uint32_t)off; off = al16(off + kb * E);
     sp->off_valA = (uint32_t)off; off = al16(off + 2 * E);
     sp->off_valB = (uint32_t)off; off = al16(off + 2 * E);
     sp->off_hist = (uint32_t)off; off = al16(off + 1024ull * W);
@@ -636,7 +642,7 @@ static bool chain_plan(int k, ChainPlan* cp, size_t* bytes)
     return nw > 0;
 }
 
-int pipeline_max_k()
+static int compute_max_k(bool wide)
 {
     // limits: sort of one pair in shared memory, 15-bit slot numbers in the
     // output ids, and a one-lane chain in shared memory
@@ -647,9 +653,15 @@ int pipeline_max_k()
         const int mid = (lo + hi + 1) / 2;
         ChainPlan cp;
         size_t cb;
-        if (sort_plan(mid, 1, &sp, &b) && chain_plan(mid, &cp, &cb)) lo = mid; else hi = mid - 1;
+        if (sort_plan(mid, 1, &sp, &b, wide) && chain_plan(mid, &cp, &cb)) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+int pipeline_max_k(bool wide)
+{
+    static const int narrow_max = compute_max_k(false), wide_max = compute_max_k(true);
+    return wide ? wide_max : narrow_max;
 }
 
 // scratch of one signal: perm, rank, sorted-order links, unwind links per
@@ -676,7 +688,7 @@ static void carve_signal(PipeParams& p, char*& w)
     p.out = (uint16_t*)w;   w += al256(2ull * np1 * kp);
 }
 
-static void fill_signal(PipeParams& p, const uint32_t* x, uint32_t* y, int32_t* argmed,
+static void fill_signal(PipeParams& p, const void* x, void* y, int32_t* argmed,
                         int64_t n, int k, int rank, bool is_float)
 {
     p = PipeParams{};
@@ -703,12 +715,14 @@ size_t pipeline_batched_workspace_bytes(const int64_t* n, const int32_t* k, int 
 cudaError_t pipeline_setup()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(sortmerge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(sortmerge_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(sortmerge_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(epilogue_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
     if ((e = cudaFuncSetAttribute(unwind_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
     if ((e = cudaFuncSetAttribute(unwind_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
     if ((e = cudaFuncSetAttribute(chain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
     if ((e = cudaFuncSetAttribute(chain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
-    return cudaFuncSetAttribute(epilogue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
+    return cudaFuncSetAttribute(epilogue_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
 }
 
 // ---------------------------------------------------------------------------
@@ -717,6 +731,7 @@ cudaError_t pipeline_setup()
 // ---------------------------------------------------------------------------
 struct ClassPlan {
     int kmax;
+    bool wide;                // 8-byte elements
     SortPlan sp;  size_t sbytes;
     UnwindPlan up; size_t ubytes; int uwarps; int bpw;
     ChainPlan cp; size_t cbytes;
@@ -731,10 +746,11 @@ static const int kBuiltinSortG[kNumTuneClasses] = {0, 0, 3, 0, 0, 0};
 static const int kBuiltinEpiG[kNumTuneClasses] = {0, 0, 4, 0, 0, 0};
 
 static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tuning* tune,
-                            ClassPlan* c)
+                            bool wide, ClassPlan* c)
 {
     const int W = kPipeThreads / 32;
     c->kmax = kmax;
+    c->wide = wide;
     // sortmerge: at most the largest G that keeps two CTAs per SM (one CTA if
     // even G = 1 does not); the class's built-in or tuned choice below that;
     // fewer when there are few pairs to spread over the SMs
@@ -742,7 +758,7 @@ static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tu
     for (int g = 1; g <= 64; ++g) {
         SortPlan t;
         size_t b;
-        if (!sort_plan(kmax, g, &t, &b)) break;
+        if (!sort_plan(kmax, g, &t, &b, wide)) break;
         if (b <= (size_t)kMaxSmemBytes / 2 || g == 1) Gcap = g;
     }
     if (Gcap == 0) return false;
@@ -753,7 +769,7 @@ static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tu
     if (tune && tune->sort_G > 0) G = min(Gcap, tune->sort_G);
     const int64_t want = (total_pairs + 2ll * num_sms - 1) / (2ll * num_sms);
     if (want >= 1 && want < G) G = (int)want;
-    sort_plan(kmax, G, &c->sp, &c->sbytes);
+    sort_plan(kmax, G, &c->sp, &c->sbytes, wide);
     c->sp.G = G;
     // unwind
     UnwindPlan& up = c->up;
@@ -775,7 +791,7 @@ static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tu
     const int GEcap = max(1, min(16, 8192 / kmax));
     c->GE = kBuiltinEpiG[cls] > 0 ? min(GEcap, kBuiltinEpiG[cls]) : GEcap;
     if (tune && tune->epi_G > 0) c->GE = min(GEcap, tune->epi_G);
-    c->ebytes = 4ull * (size_t)(c->GE + 1) * kmax;
+    c->ebytes = (wide ? 8ull : 4ull) * (size_t)(c->GE + 1) * kmax;
     return true;
 }
 
@@ -803,7 +819,10 @@ static cudaError_t launch_classes(const ClassPlan* cls, const SegTable* tabs, co
     cudaError_t e;
     TIMER_MARK(0);
     for (int c = 0; c < ncls; ++c) {
-        sortmerge_kernel<<<(unsigned)tot[c][kItemSort], kPipeThreads, cls[c].sbytes, stream>>>(tabs[c], cls[c].sp);
+        if (cls[c].wide)
+            sortmerge_kernel<uint64_t><<<(unsigned)tot[c][kItemSort], kPipeThreads, cls[c].sbytes, stream>>>(tabs[c], cls[c].sp);
+        else
+            sortmerge_kernel<uint32_t><<<(unsigned)tot[c][kItemSort], kPipeThreads, cls[c].sbytes, stream>>>(tabs[c], cls[c].sp);
         if (stats) stats->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -835,7 +854,10 @@ static cudaError_t launch_classes(const ClassPlan* cls, const SegTable* tabs, co
     }
     TIMER_MARK(3);
     for (int c = 0; c < ncls; ++c) {
-        epilogue_kernel<<<(unsigned)tot[c][kItemEpilogue], kPipeThreads, cls[c].ebytes, stream>>>(tabs[c], cls[c].GE);
+        if (cls[c].wide)
+            epilogue_kernel<uint64_t><<<(unsigned)tot[c][kItemEpilogue], kPipeThreads, cls[c].ebytes, stream>>>(tabs[c], cls[c].GE);
+        else
+            epilogue_kernel<uint32_t><<<(unsigned)tot[c][kItemEpilogue], kPipeThreads, cls[c].ebytes, stream>>>(tabs[c], cls[c].GE);
         if (stats) stats->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -844,8 +866,8 @@ static cudaError_t launch_classes(const ClassPlan* cls, const SegTable* tabs, co
     return cudaSuccess;
 }
 
-cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, int rank, bool is_float,
-                            uint32_t* y, int32_t* argmed, void* ws, size_t ws_bytes,
+cudaError_t launch_pipeline(const void* x, int64_t n, int k, int rank, Elem el,
+                            void* y, int32_t* argmed, void* ws, size_t ws_bytes,
                             int num_sms, cudaStream_t stream, LaunchStats* stats)
 {
     if (ws_bytes < pipeline_workspace_bytes(n, k)) return cudaErrorInvalidValue;
@@ -853,11 +875,11 @@ cudaError_t launch_pipeline(const uint32_t* x, int64_t n, int k, int rank, bool 
     SegTable tab{};
     tab.segs = nullptr;
     tab.nseg = 1;
-    fill_signal(tab.one, x, y, argmed, n, k, rank, is_float);
+    fill_signal(tab.one, x, y, argmed, n, k, rank, el.is_float);
     char* w = (char*)ws;
     carve_signal(tab.one, w);
     ClassPlan cls;
-    if (!make_class_plan(k, tab.one.npairs, num_sms, stats ? stats->tune : nullptr, &cls))
+    if (!make_class_plan(k, tab.one.npairs, num_sms, stats ? stats->tune : nullptr, el.wide, &cls))
         return cudaErrorInvalidValue;
     int64_t tot[1][4] = {{0, 0, 0, 0}};
     count_items(tab.one, cls, tot[0]);
@@ -877,7 +899,7 @@ int tune_class_of(int k)
     return c;
 }
 
-cudaError_t launch_pipeline_batched(const uint32_t* x, uint32_t* y, int32_t* argmed, bool is_float,
+cudaError_t launch_pipeline_batched(const void* x, void* y, int32_t* argmed, Elem el,
                                     const int64_t* x_off, const int64_t* n, const int64_t* y_off,
                                     const int32_t* k, int nseg, void* ws, size_t ws_bytes,
                                     void* stage, size_t stage_bytes, int num_sms,
@@ -907,7 +929,8 @@ cudaError_t launch_pipeline_batched(const uint32_t* x, uint32_t* y, int32_t* arg
     int cls_index[kNumClasses];
     for (int c = 0; c < kNumClasses; ++c) {
         if (!count[c]) continue;
-        if (!make_class_plan(kmax[c], pairs[c], num_sms, stats ? stats->tune : nullptr, &plans[ncls]))
+        if (!make_class_plan(kmax[c], pairs[c], num_sms, stats ? stats->tune : nullptr, el.wide,
+                             &plans[ncls]))
             return cudaErrorInvalidValue;
         cls_index[c] = ncls;
         for (int i = 0; i < 4; ++i) tot[ncls][i] = 0;
@@ -921,8 +944,9 @@ cudaError_t launch_pipeline_batched(const uint32_t* x, uint32_t* y, int32_t* arg
     for (int s = 0; s < nseg; ++s) {
         const int c = class_of(k[s]);
         PipeParams& p = host[fillpos[c]++];
-        fill_signal(p, x + x_off[s], y + y_off[s], argmed ? argmed + y_off[s] : nullptr,
-                    n[s], k[s], (k[s] - 1) / 2, is_float);
+        const int eb = el.bytes();
+        fill_signal(p, (const char*)x + x_off[s] * eb, (char*)y + y_off[s] * eb,
+                    argmed ? argmed + y_off[s] : nullptr, n[s], k[s], (k[s] - 1) / 2, el.is_float);
         carve_signal(p, w);
         count_items(p, plans[cls_index[c]], tot[cls_index[c]]);
     }

@@ -310,9 +310,10 @@ class CudaExecutor:
         return make_segments(n, k, x_off, y_off), int(n.sum()), int(m.sum()), x_off, y_off
 
     def ws_need(self, slot, jobs):
-        from . import mf_batched_workspace_bytes
+        from . import MF_FLOAT32, MF_INT32, mf_batched_workspace_bytes
         segs = self.segments(jobs)[0]
-        return mf_batched_workspace_bytes(self.handles[slot], segs)
+        code = MF_INT32 if jobs[0].dtype == "int32" else MF_FLOAT32
+        return mf_batched_workspace_bytes(self.handles[slot], segs, code)
 
     def large_of(self, k):
         from . import tier_of

@@ -14,6 +14,7 @@ configurations this library is measured on:
 * ``random_walk_f32``  -- Gaussian random walk x_{t+1} = x_t + N(0, 1),
                           accumulated in float64 and cast to float32
 * ``uniform_i32``      -- i.i.d. int32 uniform [0, 2^31)
+* ``uniform_i64``, ``random_walk_f64`` -- the 64-bit counterparts
 * ``batched_signals``  -- many float32 signals with log-uniform lengths and
                           odd window sizes, 10 % impulse noise at +-1e3
 * ``distinct_f32``     -- permutation of 0..n-1 scaled by 1e-3 plus N(0, 0.1),
@@ -65,6 +66,16 @@ def random_walk_f32(n: int, seed: int = DEFAULT_SEED) -> np.ndarray:
 def uniform_i32(n: int, seed: int = DEFAULT_SEED) -> np.ndarray:
     """i.i.d. int32 uniform on [0, 2^31): the paper's r-large generator at 32 bits."""
     return _rng(seed).integers(0, 2 ** 31, size=n, dtype=np.int64).astype(np.int32)
+
+
+def uniform_i64(n: int, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """i.i.d. int64 uniform over the whole int64 range (64-bit r-large)."""
+    return _rng(seed).integers(-2 ** 63, 2 ** 63 - 1, size=n, dtype=np.int64, endpoint=True)
+
+
+def random_walk_f64(n: int, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """Gaussian random walk x_{t+1} = x_t + N(0, 1) in float64."""
+    return np.cumsum(_rng(seed).standard_normal(n))
 
 
 def distinct_f32(n: int, seed: int = DEFAULT_SEED) -> np.ndarray:
