@@ -183,8 +183,12 @@ class ClockSampler:
 
 
 def make_signal(kind, seed):
-    from signals import random_walk_f32, uniform_i32
-    return random_walk_f32(N_SIG, seed=seed) if kind == "walk" else uniform_i32(N_SIG, seed=seed)
+    from signals import random_walk_f32, random_walk_f64, uniform_i32
+    if kind == "walk":
+        return random_walk_f32(N_SIG, seed=seed)
+    if kind == "walk64":
+        return random_walk_f64(N_SIG, seed=seed)
+    return uniform_i32(N_SIG, seed=seed)
 
 
 def cpu_oracle_rate(x, k, target_s, seed=0):
@@ -304,6 +308,10 @@ def run_ours(args):
     _, total_i, per_i, _, _, kt_i = device_run("int")
     total_i = reduce_max(dist, total_i, dev)
     value_int = weak_scaling_value(ws, m, args.steps, total_i)
+    # float64 random walk of the same length (64-bit keys)
+    _, total_d, per_d, _, _, kt_d = device_run("walk64")
+    total_d = reduce_max(dist, total_d, dev)
+    value_f64 = weak_scaling_value(ws, m, args.steps, total_d)
 
     # end to end through the host-buffer entry point (pinned host memory)
     xh = torch.from_numpy(x_walk).pin_memory()
@@ -350,6 +358,9 @@ def run_ours(args):
         "int32_uniform": {"value": value_int, "unit": UNIT,
                           "ms_per_step": total_i / args.steps,
                           "p50_ms": float(np.percentile(per_i, 50)), "kernels_ms": kt_i},
+        "float64_random_walk": {"value": value_f64, "unit": UNIT,
+                                "ms_per_step": total_d / args.steps,
+                                "p50_ms": float(np.percentile(per_d, 50)), "kernels_ms": kt_d},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N_SIG,
                 "d2h_bytes_per_step": 4 * m, "steps": e2e_steps,
                 "entry": "mf_filter_host (pinned host buffers)"},

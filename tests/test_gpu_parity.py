@@ -226,3 +226,28 @@ def test_backward_matches_oracle_gradient(handle):
     # each gx[j] sums at most k float32 terms: bound the rounding by k * eps * sum|g|
     absref = oracle.median_gradient(np.abs(g_np).astype(np.float64), ra, n)
     np.testing.assert_array_less(np.abs(gx.cpu().numpy() - ref), k * 6e-8 * absref + 1e-30)
+
+
+@pytest.mark.parametrize("n,k,kind", [(5_000_000, 1001, "walk"), (3_000_011, 20001, "int"),
+                                      (2_500_000, 31, "walk64")])
+def test_host_entry_point_chunked(handle, n, k, kind):
+    """Signals above 2^20 outputs go through the host entry point in chunks on
+    two streams; the result (and argmed, shifted per chunk) equals one device call."""
+    from signals import random_walk_f64
+    x = {"walk": lambda: random_walk_f32(n, seed=n),
+         "int": lambda: uniform_i32(n, seed=n),
+         "walk64": lambda: random_walk_f64(n, seed=n)}[kind]()
+    y = np.empty(n - k + 1, x.dtype)
+    a = np.empty(n - k + 1, np.int32)
+    mf.mf_filter_host(handle, x, k, y, a)
+    xd = torch.from_numpy(x).to(DEV)
+    yd = torch.empty(n - k + 1, dtype=xd.dtype, device=DEV)
+    ad = torch.empty(n - k + 1, dtype=torch.int32, device=DEV)
+    mf.mf_filter(handle, xd, k, yd, ad)
+    mf.mf_sync(handle)
+    assert np.array_equal(y.view(np.uint8), yd.cpu().numpy().view(np.uint8))
+    np.testing.assert_array_equal(a, ad.cpu().numpy())
+    st = np.random.default_rng(1).integers(0, n - k + 1, 200)
+    ry, ra = oracle.window_medians(x, k, st)
+    assert np.array_equal(y[st].view(np.uint8), ry.view(np.uint8))
+    np.testing.assert_array_equal(a[st].astype(np.int64), ra)
