@@ -13,14 +13,14 @@
  * sign), never by IEEE "<".  argmed[i] is the index of the median element in
  * the signal (ties between equal values resolve to the lower index, which is
  * what the paper's stable piecewise sort and its "older block first" rule in
- * Section 5.3 give).
+ * Section 6.3 give).
  *
- * Method (paper Sections 3-5): phase 1 sorts each block X_j = x[jk .. jk+k)
- * stably (Section 3 "Piecewise Sorting", Section 4.2); phase 2 walks each
+ * Method (paper Sections 3-6): phase 1 sorts each block X_j = x[jk .. jk+k)
+ * stably (Section 3 "Piecewise Sorting", Section 5.2); phase 2 walks each
  * adjacent block pair with two sorted doubly-linked lists, deleting the old
  * block's elements and undoing the deletions of the new block's elements
- * (Knuth's dancing links, Section 3 equations del / undo-del), and prints the
- * smaller of the two lists' first large elements (Section 5.2).  Both phases
+ * (Knuth's dancing links, Section 4 equations del / undo-del), and prints the
+ * smaller of the two lists' first large elements (Section 6.2).  Both phases
  * run fused in CUDA kernels; there is no CPU fallback.
  *
  * Conventions for every call below:
@@ -68,7 +68,7 @@ typedef enum {
 
 /* Element types.  Keys are compared as signed integers (int32, int64) or by
  * IEEE 754-2008 totalOrder (float32, float64; Section 5.10 of that standard);
- * the paper's experiments use 32-bit and 64-bit inputs (Section 6.3). */
+ * the paper's experiments use 32-bit and 64-bit inputs (Section 7.3). */
 typedef enum { MF_INT32 = 0, MF_FLOAT32 = 1, MF_INT64 = 2, MF_FLOAT64 = 3 } mf_dtype;
 
 /* One signal of a batch.  Offsets are in elements from the x / y base
@@ -92,7 +92,7 @@ mf_status mf_create(mf_handle* out, int device, void* cuda_stream, size_t max_wo
 /* Rebind the handle to another stream of the same device. */
 mf_status mf_set_stream(mf_handle h, void* cuda_stream);
 
-/* Median filter of one signal (paper Section 1; method Sections 3-5).
+/* Median filter of one signal (paper Section 1; method Sections 3-6).
  *  x       device pointer, n elements of `dtype` (input, not modified)
  *  n       signal length, n >= k
  *  k       odd window size, 1 <= k <= n and k <= 262,143.  Below 5001
@@ -102,7 +102,7 @@ mf_status mf_set_stream(mf_handle h, void* cuda_stream);
  *          the large-k tier: global-memory merge tiers for the
  *          block sort and the post-processing chain of each block pair split
  *          into up to 32 segments, each started from a state rebuilt with the
- *          invariant of Section 5.3 (workspace about 48 + 8 * segments bytes
+ *          invariant of Section 6.3 (workspace about 48 + 8 * segments bytes
  *          per sample)
  *  y       device pointer, n-k+1 elements of `dtype` (output, overwritten)
  *  argmed  device pointer to n-k+1 int32 (output) or NULL; needs n <= 2^31-1
@@ -116,7 +116,7 @@ mf_status mf_filter(mf_handle h, mf_dtype dtype, const void* x, int64_t n, int32
 /* Rank (order-statistic) filter: y[i] = the element of 0-based rank `rank`
  * among x[i .. i+k-1] under the (value, index) order of mf_filter, for
  * i = 0 .. n-k; argmed[i] its index.  The paper's method works unchanged for
- * any rank h in 0 .. k-1: the post-processing invariant (Section 5.3) keeps
+ * any rank h in 0 .. k-1: the post-processing invariant (Section 6.3) keeps
  * the h smallest elements of the window "small" and prints the smallest
  * large one.  rank = (k-1)/2 with odd k is mf_filter; any k >= 1 is accepted
  * here, so even k gives the lower median with rank = k/2 - 1 (the upper

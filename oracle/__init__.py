@@ -7,7 +7,7 @@ reference arm may import this package.  The CUDA library in
 ``mf_oracle.c`` is the plain definition (paper Section 1: y_i is the median of
 x_i .. x_{i+k-1}; Section 2: find the median of every window separately),
 compiled with gcc into ``oracle/_build/liboracle.so`` on first use.
-``paper_method.py`` restates the paper's own algorithm (Sections 3-5) for the
+``paper_method.py`` restates the paper's own algorithm (Sections 3-6) for the
 invariant and case-table tests; it is not used to produce expected values
 for the CUDA path.
 

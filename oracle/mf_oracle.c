@@ -21,16 +21,16 @@
  *
  * i.e. values compared first and ties broken by the element's index.  This is
  * the order the paper's method works in: its piecewise sort is stable
- * (Section 4.2, sorting the pairs (alpha[i], i) lexicographically) and, on
+ * (Section 5.2, sorting the pairs (alpha[i], i) lexicographically) and, on
  * ties between the two blocks, elements of the older block count as smaller
- * (Section 5.3).  Because equal keys mean equal bits, y is unique; the index
+ * (Section 6.3).  Because equal keys mean equal bits, y is unique; the index
  * tie-break fixes only argmed, the index of the median element.
  *
  * Values: int32 and int64 are compared as signed integers.  float32 and
  * float64 are compared by the IEEE 754-2008 totalOrder predicate (Section 5.10
  * of that standard): -NaN < -inf < negative numbers < -0 < +0 < positive
  * numbers < +inf < +NaN, NaNs ordered by payload.  The paper's experiments
- * use 32-bit and 64-bit inputs (Section 6.3).  The paper only uses integers (Section 6.2); IEEE "<"
+ * use 32-bit and 64-bit inputs (Section 7.3).  The paper only uses integers (Section 7.2); IEEE "<"
  * would make -0 and +0 equal and let the result's bits depend on which of the
  * two was picked, so the oracle never uses it.
  *

@@ -3,17 +3,17 @@
 Restates, for the tests, the two-phase method of "Median Filtering is
 Equivalent to Sorting" (Suomela):
 
-* Section 3 / Section 5.1 -- piecewise stable sort: each block X_j of length
+* Section 3 / Section 6.1 -- piecewise stable sort: each block X_j of length
   k = 2h + 1 gets the permutation P_j that sorts the pairs (X_j[i], i).
-* Section 4 -- the block data structure: a sorted doubly-linked list over the
+* Section 5 -- the block data structure: a sorted doubly-linked list over the
   block's indices with a sentinel node k, arrays prev/next of length k + 1,
   a counter s of "small" elements and a pointer m to the first large one
-  (Section 4.3 invariants: next[k] = p_0, prev[k] = p_{c-1}, m = p_s).
+  (Section 5.3 invariants: next[k] = p_0, prev[k] = p_{c-1}, m = p_s).
   Operations construct / delete / undelete / unwind / advance / small / peek
   (Figures "Block data structure interface" and "... implementation").
-* Section 5.2 -- post-processing: for each adjacent pair of blocks, delete
+* Section 6.2 -- post-processing: for each adjacent pair of blocks, delete
   the old block's elements in index order while undoing the new block's
-  deletions (Knuth's dancing links, Section 3 equations del / undo-del),
+  deletions (Knuth's dancing links, Section 4 equations del / undo-del),
   advance one pointer whenever s_A + s_B < h, and print min(peek A, peek B).
 
 Readings of the paper used here (each also listed in the design notes):
@@ -24,9 +24,9 @@ Readings of the paper used here (each also listed in the design notes):
   pair emits r outputs (the paper calls the extension "straightforward").
 * Ties: the stable sort orders equal values by index inside a block, and
   peek(A) <= peek(B) advances A, so equal values of the older block count as
-  smaller (Section 5.3).
+  smaller (Section 6.3).
 
-It is used to pin the invariant of Section 5.3 (s_A + s_B = h and
+It is used to pin the invariant of Section 6.3 (s_A + s_B = h and
 S_A u S_B = H_AB before every output), the seven cases of the case-analysis
 table, and properly nested delete/undelete.  Expected values for the CUDA
 path always come from the plain definition in ``mf_oracle.c``.

@@ -1,12 +1,12 @@
 // mf_device.cuh -- device building blocks shared by the median-filter kernels.
 //
 // Paper: "Median Filtering is Equivalent to Sorting" (Suomela).
-//  * order keys ............ Section 4.2 (the stable sort compares (alpha[i], i))
-//  * warp radix sort ....... Section 3 "Piecewise Sorting" / Section 5.1
+//  * order keys ............ Section 5.2 (the stable sort compares (alpha[i], i))
+//  * warp radix sort ....... Section 3 "Piecewise Sorting" / Section 6.1
 //  * pair merge ............ joint ranks of the two blocks of a pair: the
-//                            rank-space form of the comparisons of Section 4.3
+//                            rank-space form of the comparisons of Section 5.3
 //                            ("(alpha[i], i) < (alpha[m], m)") and of the
-//                            post-processing (peek(A) <= peek(B), Section 5.2)
+//                            post-processing (peek(A) <= peek(B), Section 6.2)
 #pragma once
 #include <cstdint>
 
@@ -45,7 +45,7 @@ __device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
 // shared memory (phase 1, piecewise sort).  The group holds `cnt` elements:
 // keys kin[0..cnt) and values vin[0..cnt) = CTA-local element indices, which
 // start in ascending order, so LSD stability orders equal keys by index --
-// the stable sort of (alpha[i], i) of Section 4.2.  Four 8-bit key passes;
+// the stable sort of (alpha[i], i) of Section 5.2.  Four 8-bit key passes;
 // when the group holds more than one block, a final pass on the block number
 // (vin - e0) / k regroups the elements block by block.  A pass whose digits
 // are all equal is skipped (common for the high bytes of smooth signals).
@@ -156,8 +156,8 @@ inline __device__ void warp_sort_group(KeyT* kin, uint16_t* vin, KeyT* kt, uint1
 // ---------------------------------------------------------------------------
 // Joint ranks of one block pair (A = older block, B = newer block): merging
 // the two sorted blocks, with A first on equal keys, gives every element of
-// A u B its rank in the window order; "alpha[i] is small" (Section 4.3) and
-// peek(A) <= peek(B) (Section 5.2) become comparisons of these ranks.
+// A u B its rank in the window order; "alpha[i] is small" (Section 5.3) and
+// peek(A) <= peek(B) (Section 6.2) become comparisons of these ranks.
 // Warp-cooperative merge path: lane L emits merged positions
 // [L*per, (L+1)*per).  Results are stored by position (jposA / jposB).
 // ---------------------------------------------------------------------------

@@ -7,7 +7,7 @@
 // A u B, A first on ties), with 32-bit indices and the data in global memory:
 //
 //   large_chunk_sort  a warp sorts each 1024-element chunk of a block in
-//                     shared memory (stable LSD radix, Section 5.1)
+//                     shared memory (stable LSD radix, Section 6.1)
 //   large_merge       global merge-path tiers: sorted runs of R -> 2R until a
 //                     run covers the block, left run first on equal keys
 //   large_ranks       rank of each position in its block
@@ -21,7 +21,7 @@
 //   large_seginit     rebuilds the lists before step i0 of a pair (Section
 //                     5.3 invariant: S_A u S_B are the h smallest of the
 //                     window) from bitsets of the window's joint ranks
-//   large_chain       the steps i0 .. i1-1 of Section 5.2 from that state,
+//   large_chain       the steps i0 .. i1-1 of Section 6.2 from that state,
 //                     one thread per (pair, segment), lists in global memory
 //   large_epilogue    node -> input element, y / argmed
 //
@@ -283,7 +283,7 @@ large_unwind(LargeParams p, const uint32_t* __restrict__ vs, int nw, int ns)
 // The window is A's positions >= i0 and B's positions < i0.  KA / KB mark
 // the joint ranks of its A and B elements; a node's list neighbours are the
 // nearest marked ranks of its own block, and the small elements are the
-// window's h smallest (Section 5.3 invariant), found by a prefix count.
+// window's h smallest (Section 6.3 invariant), found by a prefix count.
 __global__ void __launch_bounds__(256)
 large_seginit(LargeParams p, int nw, int ns)
 {
@@ -405,7 +405,7 @@ large_seginit(LargeParams p, int nw, int ns)
     }
 }
 
-// Section 5.2, steps i0 .. i1-1 of pair q: delete(A, i), undelete(B, i),
+// Section 6.2, steps i0 .. i1-1 of pair q: delete(A, i), undelete(B, i),
 // advance while s_A + s_B < h, print min(peek A, peek B).  mA is always a
 // node of A's list (joint rank ja) and mB of B's (jb); sentinels rank last.
 __global__ void __launch_bounds__(32)

@@ -2,21 +2,21 @@
 //
 // Paper: "Median Filtering is Equivalent to Sorting" (Suomela).
 //
-// The post-processing of a block pair (Section 5.2) is a chain of k dependent
+// The post-processing of a block pair (Section 6.2) is a chain of k dependent
 // steps whose lists must sit in shared memory; how many chains an SM can run
 // at once -- shared-memory bytes per chain -- sets the speed.  So everything
 // that is not the chain runs in separate, fully parallel kernels, and the
 // chain kernel keeps nothing in shared memory but the lists:
 //
-//   sortmerge_kernel  load x, stable sort of every block (Section 4.2), and
+//   sortmerge_kernel  load x, stable sort of every block (Section 5.2), and
 //                     per block: perm (pi), rank (pi^-1) and the sorted-order
-//                     links in position space (construct, Section 4.3); per
+//                     links in position space (construct, Section 5.3); per
 //                     pair: the rank of every element in the merged order of
 //                     the pair's two blocks ("joint rank", A first on ties).
 //   unwind_kernel     per block used as B: the links unwind(B) leaves behind
-//                     (Section 3, "Unwind"); one lane per block.
+//                     (Section 4, "Unwind"); one lane per block.
 //   chain_kernel      one lane per pair: delete(A, i), undelete(B, i),
-//                     advance, print min(peek) for every step (Section 5.2),
+//                     advance, print min(peek) for every step (Section 6.2),
 //                     lists in shared memory.
 //   epilogue_kernel   node -> input element, coalesced stores of y / argmed.
 //
@@ -24,8 +24,8 @@
 // until step i deletes it, and position i of B from the moment step i
 // undeletes it (A only ever holds positions > i, B only positions <= i), plus
 // two sentinels k (A) and k+1 (B) -- the paper's arrays of length k+1
-// (Section 4.3), shared by A and B.  Comparisons use the joint rank of the
-// node's element (the pi^-1 form of Section 4.2, extended across the pair),
+// (Section 5.3), shared by A and B.  Comparisons use the joint rank of the
+// node's element (the pi^-1 form of Section 5.2, extended across the pair),
 // so "alpha[i] is small" is jr(i) < jr(m) and peek(A) <= peek(B) is
 // jr(mA) < jr(mB); the sentinels have rank 0xFFFF, above every element.
 #include <cuda_runtime.h>
@@ -153,7 +153,7 @@ sortmerge_kernel(SegTable tab, SortPlan sp)
 
 // ===========================================================================
 // unwind_kernel: links of every block j >= 1 (block j is B of pair j).
-// unwind(B) (Section 3, "Unwind") deletes positions NB-1 .. 0; when position
+// unwind(B) (Section 4, "Unwind") deletes positions NB-1 .. 0; when position
 // i is deleted its list holds exactly positions 0..i, so the prev / next it
 // keeps are the nearest smaller / larger element among positions < i.
 // Walking positions upward with a bitset of the ranks seen so far gives the
@@ -296,7 +296,7 @@ unwind_kernel(SegTable tab, UnwindPlan up)
 }
 
 // ===========================================================================
-// chain_kernel: the post-processing of Section 5.2, one lane per block pair.
+// chain_kernel: the post-processing of Section 6.2, one lane per block pair.
 // Shared memory per lane (bank-private, word index x * NL + lane):
 //   rec[0 .. k+1]   prev:16 | next:16 (node numbers = slots, see top)
 //   jr [0 .. k+1]   joint rank of the node's current element (u16, two per word)
@@ -312,7 +312,7 @@ unwind_kernel(SegTable tab, UnwindPlan up)
 // i and prev(next(i)) is i; when undelete(B, i) relinks i between p and n,
 // next(p) is n and prev(n) is p.  So in the packed format each relink is one
 // XOR of old ^ new into the field; in the wide format it is a 16-bit store
-// (equations del / undo-del of Section 3).
+// (equations del / undo-del of Section 4).
 template <bool PACKED>
 struct Lists {
     static constexpr int PSH = PACKED ? 10 : 16;
@@ -346,7 +346,7 @@ struct Lists {
     }
 };
 
-// State of the two block data structures (Section 4.3): m, its list word,
+// State of the two block data structures (Section 5.3): m, its list word,
 // its joint rank, and s.
 struct PairState {
     uint32_t mA, wmA, rmA;
@@ -354,7 +354,7 @@ struct PairState {
     int sA, sB;
 };
 
-// One step i of the post-processing (Section 5.2), branch-free: delete(A, i),
+// One step i of the post-processing (Section 6.2), branch-free: delete(A, i),
 // undelete(B, i), advance if s_A + s_B < h, return the printed node
 // (isB << 15 | slot).  wa is slot i's current word (loaded after the previous
 // step's last store); the next step's word is loaded into *wnext.

@@ -6,7 +6,7 @@ parity check -- the CPU oracle under ``oracle/`` and the CUDA library in
 ``paper_1406_1717_gb300/`` -- receive their inputs from here, so they always
 see identical bits.  Neither side imports the other.
 
-Generators follow the workloads of the paper's experiments (Section 6.3 lists
+Generators follow the workloads of the paper's experiments (Section 7.3 lists
 asc, desc, r-asc, r-desc, r-large, r-small and r-block) plus the five
 configurations this library is measured on:
 
@@ -56,7 +56,7 @@ def random_walk_f32(n: int, seed: int = DEFAULT_SEED) -> np.ndarray:
 
     The cumulative sum is taken in float64 and cast to float32 at the end, so
     the walk does not accumulate float32 rounding drift.  Locally the signal
-    is near-sorted: the paper's benign case (Section 6.3, r-asc / r-desc).
+    is near-sorted: the paper's benign case (Section 7.3, r-asc / r-desc).
     """
     steps = _rng(seed).standard_normal(n)
     steps[0] = 0.0
@@ -101,14 +101,14 @@ def distinct_f32(n: int, seed: int = DEFAULT_SEED) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
-# the seven generators of the paper's Section 6.3
+# the seven generators of the paper's Section 7.3
 # ----------------------------------------------------------------------------
 PAPER_GENERATORS = ("asc", "desc", "r-asc", "r-desc", "r-large", "r-small", "r-block")
 
 
 def paper_generator(name: str, n: int, seed: int = DEFAULT_SEED,
                     dtype: str = "int32") -> np.ndarray:
-    """The input generators listed in the paper's Section 6.3.
+    """The input generators listed in the paper's Section 7.3.
 
     Integer versions follow the stated ranges.  ``r-block`` is under-specified
     in the paper ("piecewise constant data + small uniform random noise"); the

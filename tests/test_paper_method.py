@@ -1,10 +1,10 @@
 """Pins of the paper-method CPU reference (oracle/paper_method.py).
 
-* Section 4.1: deletions and undeletions must be properly nested; undoing
+* Section 5.1: deletions and undeletions must be properly nested; undoing
   them in reverse order restores the list exactly.
-* Section 5.3, equation (inv): before every output s_A + s_B = h and
+* Section 6.3, equation (inv): before every output s_A + s_B = h and
   S_A u S_B = H_AB (the h smallest elements of the window).
-* Section 5.3, Lemma 1 and its case-analysis table: with S_A non-empty, the
+* Section 6.3, Lemma 1 and its case-analysis table: with S_A non-empty, the
   small sets after delete/undelete and after the advance follow one of the
   table's rows.  Reading of the table used here: the first group holds when
   the deleted a_A is small (a_A <= p_A), the second when it is large
@@ -30,7 +30,7 @@ def test_properly_nested_delete_undelete_restores_list():
     alpha = list(rng.integers(0, 50, size=31))
     blk = SortedBlock(alpha, 15)
     before = (list(blk.prev), list(blk.next), blk.members())
-    # the example of Section 4.1: delete 15, delete 3, undelete 3, undelete 15
+    # the example of Section 5.1: delete 15, delete 3, undelete 3, undelete 15
     blk._unlink(15)
     blk._unlink(3)
     assert 15 not in blk.members() and 3 not in blk.members()
