@@ -102,7 +102,7 @@ mf_status mf_set_stream(mf_handle h, void* cuda_stream);
  *          the large-k tier: global-memory merge tiers for the
  *          block sort and the post-processing chain of each block pair split
  *          into up to 32 segments, each started from a state rebuilt with the
- *          invariant of Section 6.3 (workspace about 48 + 8 * segments bytes
+ *          invariant of Section 6.3 (workspace about 52 + 16 * segments bytes
  *          per sample)
  *  y       device pointer, n-k+1 elements of `dtype` (output, overwritten)
  *  argmed  device pointer to n-k+1 int32 (output) or NULL; needs n <= 2^31-1

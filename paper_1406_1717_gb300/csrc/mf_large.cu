@@ -1,10 +1,9 @@
 // mf_large.cu -- the median filter for window sizes too large for the
 // shared-memory pipeline (pipeline_max_k() < k <= kLargeMaxK).
 //
-// Paper: "Median Filtering is Equivalent to Sorting" (Suomela).  Same method
-// and node numbering as mf_pipeline.cu (slot i = A's position i until step i,
-// then B's position i; sentinels k and k+1; comparisons by joint rank in
-// A u B, A first on ties), with 32-bit indices and the data in global memory:
+// Paper: "Median Filtering is Equivalent to Sorting" (Suomela).  The method
+// of mf_pipeline.cu (comparisons by joint rank in A u B, A first on ties)
+// with 32-bit indices and the data in global memory:
 //
 //   large_chunk_sort  a warp sorts each 1024-element chunk of a block in
 //                     shared memory (stable LSD radix, Section 6.1)
@@ -12,24 +11,30 @@
 //                     run covers the block, left run first on equal keys
 //   large_ranks       rank of each position in its block
 //   large_jrank       joint ranks of each pair by binary search in the other
-//                     block: ja / jb by position and M = the merged order
+//                     block: ja / jb by position, jrs by B's sorted order and
+//                     M = the merged order
 //   large_unwind      unwind(B)'s links (Section 4: after unwind, undelete(B, i)
 //                     relinks i between its nearest smaller and larger
 //                     elements among positions < i); one CTA per run of
 //                     positions, seeded with a rank bitset of the positions
 //                     before the run
-//   large_seginit     rebuilds the lists before step i0 of a pair (Section
-//                     5.3 invariant: S_A u S_B are the h smallest of the
-//                     window) from bitsets of the window's joint ranks
+//   large_seginit     rebuilds the lists before step i0 of a pair (Section 6.3
+//                     invariant: S_A u S_B are the h smallest of the window)
+//                     from bitsets of the window's joint ranks
 //   large_chain       the steps i0 .. i1-1 of Section 6.2 from that state,
 //                     one thread per (pair, segment), lists in global memory
 //   large_epilogue    node -> input element, y / argmed
 //
+// Nodes are numbered by joint rank: the element of joint rank r is node r,
+// A's sentinel is 2k and B's 2k+1.  A node's number is its rank, so "is
+// small" and peek(A) <= peek(B) compare node numbers, and list neighbours are
+// rank neighbours: the walks of the two m pointers stay within a few cache
+// lines, and the only random load of a step (the deleted node, known in
+// advance) is prefetched.
 // The serial depth of one pair is k steps; splitting the k steps of a pair
 // into S independent segments, each starting from a state rebuilt with O(k)
 // parallel work, cuts the depth to k / S at the price of S private copies of
-// the pair's links (8 bytes per node; joint ranks stay in shared per-pair
-// arrays because a node's rank only depends on which block it holds).
+// the pair's links (8 bytes per node, 2k + 2 nodes).
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "mf_device.cuh"
@@ -40,7 +45,6 @@ namespace mf {
 constexpr int kChunk = 1024;                     // elements per warp sort
 constexpr int kUnwindRun = 1024;                 // positions per unwind CTA
 constexpr uint32_t kBFlag = 0x80000000u;          // node id of B's element
-constexpr uint32_t kInf = 0xffffffffu;           // joint rank of the sentinels
 
 struct LargeParams {
     const void* x;                               // 4- or 8-byte elements
@@ -51,17 +55,18 @@ struct LargeParams {
     int64_t kp;                                  // row stride (k rounded up to 32)
     bool is_float;
     int S, L;                                    // segments per pair, steps per segment
-    int64_t LS;                                  // list stride: k + 2 rounded up to 32
+    int64_t LN;                                  // list stride: 2k + 2 rounded up to 32
     void *keyA, *keyB;                           // [nblocks][kp] sort keys (4 or 8 bytes)
     uint32_t *valA, *valB;                       // [nblocks][kp] positions (ping-pong)
     uint32_t* rnk;                               // [nblocks][kp] rank of position p
     uint2* ulink;                                // [nblocks][kp] unwind (prev, next), sentinel k+1
     uint32_t* ja;                                // [npairs][kp] joint rank of A's position p
     uint32_t* jb;                                // [npairs][kp] joint rank of B's position p
+    uint32_t* jrs;                               // [npairs][kp] joint rank of B's t-th smallest
     uint32_t* M;                                 // [npairs][2 kp] node at joint rank r
     uint32_t* out;                               // [npairs][kp] printed node at step i
     int4* seg;                                   // [npairs][S] (mA, mB, sA, sB) before step i0
-    uint2* lists;                                // [npairs][S][LS] (next, prev) per node
+    uint2* lists;                                // [npairs][S][LN] (next, prev) per rank node
 };
 
 __device__ __forceinline__ int block_len(const LargeParams& p, int64_t b) {
@@ -223,6 +228,7 @@ large_jrank(LargeParams p, const KeyT* __restrict__ ks, const uint32_t* __restri
         const uint32_t pos = vs[bbase + u];
         M[u + lo] = kBFlag | pos;
         p.jb[q * p.kp + pos] = (uint32_t)(u + lo);
+        p.jrs[q * p.kp + u] = (uint32_t)(u + lo);
     }
 }
 
@@ -270,11 +276,13 @@ large_unwind(LargeParams p, const uint32_t* __restrict__ vs, int nw, int ns)
         }
     }
     __syncthreads();
-    const uint32_t sentB = (uint32_t)p.k + 1;
+    // block ranks -> rank nodes of pair b-1 (B's t-th smallest is node jrs[t])
+    const uint32_t sentB = 2u * (uint32_t)p.k + 1u;
+    const uint32_t* jrs = p.jrs + (b - 1) * p.kp;
     for (int t = threadIdx.x; t < len; t += blockDim.x) {
         const int2 q = pp[t];
-        const uint32_t pv = q.x >= 0 ? __ldg(vs + base + q.x) : sentB;
-        const uint32_t nx = q.y >= 0 ? __ldg(vs + base + q.y) : sentB;
+        const uint32_t pv = q.x >= 0 ? __ldg(jrs + q.x) : sentB;
+        const uint32_t nx = q.y >= 0 ? __ldg(jrs + q.y) : sentB;
         p.ulink[base + i0 + t] = make_uint2(pv, nx);
     }
 }
@@ -295,7 +303,6 @@ large_seginit(LargeParams p, int nw, int ns)
     const int i0 = s * p.L;
     if (i0 >= NB) return;
     const int k = p.k, h = p.h, tot = k + NB;
-    const uint32_t SA = (uint32_t)k, SB = (uint32_t)k + 1;
     uint32_t* KA = sw;
     uint32_t* KB = KA + nw;
     uint32_t* KA1 = KB + nw;
@@ -363,54 +370,45 @@ large_seginit(LargeParams p, int nw, int ns)
         }
     }
     __syncthreads();
-    uint2* Lq = p.lists + sid * p.LS;
-    const uint32_t* JA = p.ja + q * p.kp;
-    const uint32_t* JB = p.jb + q * p.kp;
-    auto node = [&](int r, uint32_t sent) -> uint32_t {
-        return r >= 0 ? (__ldg(M + r) & ~kBFlag) : sent;
-    };
+    // lists of the window in rank-node space: a kept node's neighbours are the
+    // nearest kept ranks of its own block; sentinels SA = 2k, SB = 2k+1
+    uint2* Lq = p.lists + sid * p.LN;
+    const uint32_t SA = 2u * (uint32_t)k, SB = SA + 1u;
     if (threadIdx.x == 0) {
         const int T = sh_state[0], sA = sh_state[1];
-        const uint32_t mA = node(bits_first_from(KA, KA1, nw, ns, T), SA);
-        const uint32_t mB = node(bits_first_from(KB, KB1, nw, ns, T), SB);
-        p.seg[sid] = make_int4((int)mA, (int)mB, sA, h - sA);
-        Lq[SA] = make_uint2(node(bits_first_from(KA, KA1, nw, ns, 0), SA),
-                            node(bits_last_before(KA, KA1, nw, tot), SA));
-        Lq[SB] = make_uint2(node(bits_first_from(KB, KB1, nw, ns, 0), SB),
-                            node(bits_last_before(KB, KB1, nw, tot), SB));
+        const int fa = bits_first_from(KA, KA1, nw, ns, T), fb = bits_first_from(KB, KB1, nw, ns, T);
+        p.seg[sid] = make_int4(fa >= 0 ? fa : (int)SA, fb >= 0 ? fb : (int)SB, sA, h - sA);
+        const int a0 = bits_first_from(KA, KA1, nw, ns, 0), a1 = bits_last_before(KA, KA1, nw, tot);
+        const int b0 = bits_first_from(KB, KB1, nw, ns, 0), b1 = bits_last_before(KB, KB1, nw, tot);
+        Lq[SA] = make_uint2(a0 >= 0 ? (uint32_t)a0 : SA, a1 >= 0 ? (uint32_t)a1 : SA);
+        Lq[SB] = make_uint2(b0 >= 0 ? (uint32_t)b0 : SB, b1 >= 0 ? (uint32_t)b1 : SB);
     }
-    // each thread handles 4 slots per round so that their global loads overlap
-    constexpr int U = 4;
-    for (int j0 = threadIdx.x; j0 < k; j0 += U * blockDim.x) {
-        int r[U], nx[U], pv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int j = j0 + u * (int)blockDim.x;
-            r[u] = j < k ? (int)__ldg((j >= i0 ? JA : JB) + j) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int j = j0 + u * (int)blockDim.x;
-            const bool a = j >= i0;
-            nx[u] = bits_first_from(a ? KA : KB, a ? KA1 : KB1, nw, ns, r[u] + 1);
-            pv[u] = bits_last_before(a ? KA : KB, a ? KA1 : KB1, nw, r[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int j = j0 + u * (int)blockDim.x;
-            const uint32_t sent = j >= i0 ? SA : SB;
-            const uint2 v = make_uint2(node(nx[u], sent), node(pv[u], sent));
-            if (j < k) Lq[j] = v;
-        }
+    for (int r = threadIdx.x; r < tot; r += blockDim.x) {
+        const uint32_t bit = 1u << (r & 31);
+        const bool inA = (KA[r >> 5] & bit) != 0, inB = (KB[r >> 5] & bit) != 0;
+        if (!inA && !inB) continue;                  // not in the window: never read
+        const uint32_t* W = inA ? KA : KB;
+        const uint32_t* W1 = inA ? KA1 : KB1;
+        const uint32_t sent = inA ? SA : SB;
+        const int nx = bits_first_from(W, W1, nw, ns, r + 1);
+        const int pv = bits_last_before(W, W1, nw, r);
+        Lq[r] = make_uint2(nx >= 0 ? (uint32_t)nx : sent, pv >= 0 ? (uint32_t)pv : sent);
     }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* ptr)
+{
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(ptr));
+}
+
 // Section 6.2, steps i0 .. i1-1 of pair q: delete(A, i), undelete(B, i),
-// advance while s_A + s_B < h, print min(peek A, peek B).  mA is always a
-// node of A's list (joint rank ja) and mB of B's (jb); sentinels rank last.
+// advance while s_A + s_B < h, print min(peek A, peek B).  Node numbers are
+// joint ranks, so "is small" and the peek comparison compare node numbers;
+// the sentinels 2k (A) and 2k+1 (B) rank above every element.
 __global__ void __launch_bounds__(32)
 large_chain(LargeParams p)
 {
+    constexpr int kAhead = 8;                      // prefetch distance in steps
     const int64_t sid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (sid >= p.npairs * p.S) return;
     const int64_t q = sid / p.S;
@@ -420,9 +418,8 @@ large_chain(LargeParams p)
     if (i0 >= NB) return;
     const int i1 = min(i0 + p.L, NB);
     const int h = p.h;
-    const uint32_t k = (uint32_t)p.k;
-    uint2* Lq = p.lists + sid * p.LS;
-    uint32_t* NXp = reinterpret_cast<uint32_t*>(Lq);       // next of node j at [2j]
+    uint2* Lq = p.lists + sid * p.LN;
+    uint32_t* NXp = reinterpret_cast<uint32_t*>(Lq);       // next of node r at [2r], prev at [2r+1]
     const uint32_t* JA = p.ja + q * p.kp;
     const uint32_t* JB = p.jb + q * p.kp;
     const uint2* UL = p.ulink + (q + 1) * p.kp;
@@ -430,45 +427,36 @@ large_chain(LargeParams p)
     const int4 st = p.seg[sid];
     uint32_t mA = (uint32_t)st.x, mB = (uint32_t)st.y;
     int sA = st.z, sB = st.w;
-    uint32_t jmA = mA < k ? __ldg(JA + mA) : kInf;
-    uint32_t jmB = mB < k ? __ldg(JB + mB) : kInf;
-    uint32_t ra = __ldg(JA + i0), rb = __ldg(JB + i0);
-    uint2 u = __ldg(UL + i0);
+    for (int t = i0; t < min(i0 + kAhead, i1); ++t) prefetch_l2(Lq + __ldg(JA + t));
     for (int i = i0; i < i1; ++i) {
-        const uint32_t ui = (uint32_t)i;
-        const uint2 Li = Lq[i];
+        const uint32_t a = __ldg(JA + i), b = __ldg(JB + i);
+        const uint2 u = __ldg(UL + i);
+        if (i + kAhead < i1) prefetch_l2(Lq + __ldg(JA + i + kAhead));
+        const uint2 La = Lq[a];
         const uint2 LmA = Lq[mA];
         const uint2 LmB = Lq[mB];
-        uint32_t ra_n = 0, rb_n = 0;
-        uint2 u_n = make_uint2(0, 0);
-        if (i + 1 < i1) { ra_n = __ldg(JA + i + 1); rb_n = __ldg(JB + i + 1); u_n = __ldg(UL + i + 1); }
-        // delete(A, i): unlink, then keep s_A and m consistent
-        const uint32_t na = Li.x, pa = Li.y;
+        // delete(A, i): unlink node a, then keep s_A and m consistent
+        const uint32_t na = La.x, pa = La.y;
         NXp[2 * pa] = na;
         NXp[2 * na + 1] = pa;
-        if (ra < jmA) {
+        if (a < mA) {
             --sA;
         } else {
             uint32_t pvm = (mA == na) ? pa : LmA.y;        // prev of m after the unlink
-            if (mA == ui) { mA = na; pvm = pa; }
+            if (mA == a) { mA = na; pvm = pa; }
             if (sA > 0) { mA = pvm; --sA; }
-            jmA = mA < k ? __ldg(JA + mA) : kInf;
         }
-        // undelete(B, i): slot i now holds B's element i
-        Lq[i] = make_uint2(u.y, u.x);
-        NXp[2 * u.x] = ui;
-        NXp[2 * u.y + 1] = ui;
-        if (rb < jmB) {
-            mB = (mB == u.y) ? ui : LmB.y;
-            jmB = mB < k ? __ldg(JB + mB) : kInf;
-        }
+        // undelete(B, i): relink node b between its unwind links
+        Lq[b] = make_uint2(u.y, u.x);
+        NXp[2 * u.x] = b;
+        NXp[2 * u.y + 1] = b;
+        if (b < mB) mB = (mB == u.y) ? b : LmB.y;
         // advance the smaller peek while s_A + s_B < h
         if (sA + sB < h) {
-            if (jmA < jmB) { mA = Lq[mA].x; ++sA; jmA = mA < k ? __ldg(JA + mA) : kInf; }
-            else           { mB = Lq[mB].x; ++sB; jmB = mB < k ? __ldg(JB + mB) : kInf; }
+            if (mA < mB) { mA = Lq[mA].x; ++sA; }
+            else         { mB = Lq[mB].x; ++sB; }
         }
-        OUT[i] = jmA < jmB ? mA : (kBFlag | mB);
-        ra = ra_n; rb = rb_n; u = u_n;
+        OUT[i] = mA < mB ? mA : mB;                        // joint rank of the median
     }
 }
 
@@ -484,7 +472,8 @@ large_epilogue(LargeParams p, const uint32_t* __restrict__ vs)
         src = vs[p.h];                           // y[0] = X_0[P_0[h]]
     } else {
         const int64_t q = (o - 1) / p.k, i = (o - 1) - q * p.k;
-        const uint32_t id = p.out[q * p.kp + i];
+        const uint32_t r = p.out[q * p.kp + i];                 // joint rank in pair q
+        const uint32_t id = __ldg(p.M + q * 2 * p.kp + r);
         src = (q + (id >> 31)) * (int64_t)p.k + (id & ~kBFlag);
     }
     reinterpret_cast<ValT*>(p.y)[o] = __ldg(reinterpret_cast<const ValT*>(p.x) + src);
@@ -495,7 +484,7 @@ large_epilogue(LargeParams p, const uint32_t* __restrict__ vs)
 static inline uint64_t a256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
 
 struct LargeShape {
-    int64_t nblocks, npairs, kp, LS;
+    int64_t nblocks, npairs, kp, LN;
     int S, L;
 };
 
@@ -505,7 +494,7 @@ static LargeShape large_shape(int64_t n, int k)
     s.nblocks = (n + k - 1) / k;
     s.npairs = s.nblocks - 1;
     s.kp = ((int64_t)k + 31) & ~int64_t(31);
-    s.LS = ((int64_t)k + 2 + 31) & ~int64_t(31);
+    s.LN = (2 * (int64_t)k + 2 + 31) & ~int64_t(31);
     int S = (k + kLargeSegSteps - 1) / kLargeSegSteps;
     S = S < 1 ? 1 : (S > kLargeMaxSegs ? kLargeMaxSegs : S);
     s.S = S;
@@ -539,7 +528,8 @@ size_t large_workspace_bytes(int64_t n, int k, bool wide)
     b += a256(4ull * np1 * kp) * 3;                          // ja jb out
     b += a256(8ull * np1 * kp);                              // M
     b += a256(16ull * np1 * s.S);                            // seg
-    b += a256(8ull * np1 * s.S * (uint64_t)s.LS);            // lists
+    b += a256(4ull * np1 * kp);                              // jrs
+    b += a256(8ull * np1 * s.S * (uint64_t)s.LN);            // lists
     return (size_t)b;
 }
 
@@ -639,7 +629,7 @@ cudaError_t launch_large(const void* x, int64_t n, int k, int rank, Elem el, voi
     p.n = n; p.k = k; p.h = rank;
     p.nblocks = sh.nblocks; p.npairs = sh.npairs; p.kp = sh.kp;
     p.is_float = el.is_float;
-    p.S = sh.S; p.L = sh.L; p.LS = sh.LS;
+    p.S = sh.S; p.L = sh.L; p.LN = sh.LN;
     const uint64_t nb = (uint64_t)sh.nblocks, kp = (uint64_t)sh.kp;
     const uint64_t np1 = (uint64_t)(sh.npairs > 0 ? sh.npairs : 1);
     const uint64_t kb = (uint64_t)el.bytes();
@@ -652,6 +642,7 @@ cudaError_t launch_large(const void* x, int64_t n, int k, int rank, Elem el, voi
     p.ulink = (uint2*)w;   w += a256(8ull * nb * kp);
     p.ja = (uint32_t*)w;   w += a256(4ull * np1 * kp);
     p.jb = (uint32_t*)w;   w += a256(4ull * np1 * kp);
+    p.jrs = (uint32_t*)w;  w += a256(4ull * np1 * kp);
     p.out = (uint32_t*)w;  w += a256(4ull * np1 * kp);
     p.M = (uint32_t*)w;    w += a256(8ull * np1 * kp);
     p.seg = (int4*)w;      w += a256(16ull * np1 * sh.S);
