@@ -9,6 +9,7 @@
 //                            post-processing (peek(A) <= peek(B), Section 6.2)
 #pragma once
 #include <cstdint>
+#include "mf_internal.h"
 
 namespace mf {
 
@@ -192,5 +193,30 @@ inline __device__ void warp_merge_ranks(const KeyT* kA, const uint16_t* vA, int 
         }
     }
 }
+
+// ===========================================================================
+// Signals and work items.  Every kernel works on items (sortmerge,
+// sortlist and epilogue: CTAs of G consecutive block pairs; unwind: warp groups of blocks;
+// chain: block pairs).  A launch covers one signal (descriptor passed by
+// value) or a batch of signals (device table; each descriptor carries the
+// index of its first item in every kernel, and an item finds its signal by
+// binary search).
+// ===========================================================================
+enum { kItemSort = 0, kItemUnwind = 1, kItemChain = 2, kItemEpilogue = 3 };
+
+__device__ __forceinline__ PipeParams find_signal(const SegTable& t, int kern, int64_t item,
+                                                  int64_t* local)
+{
+    if (t.segs == nullptr) { *local = item; return t.one; }
+    int lo = 0, hi = t.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.segs[mid].start[kern] <= item) lo = mid; else hi = mid - 1;
+    }
+    const PipeParams p = t.segs[lo];
+    *local = item - p.start[kern];
+    return p;
+}
+
 
 }  // namespace mf

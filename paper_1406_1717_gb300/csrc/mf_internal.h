@@ -25,6 +25,13 @@ struct PipeParams {
     uint16_t* ja;             // [npairs][kp] joint rank of A's position p
     uint16_t* jb;             // [npairs][kp] joint rank of B's position p
     uint16_t* out;            // [npairs][kp] printed node at step i: isB << 15 | slot
+    // fused path (sortlist_kernel; 4-byte elements, k <= kFusedMaxK)
+    uint32_t* wA;             // [npairs][kw] list words of construct(A): slots 0..k+1, m_A in slot k+2
+    uint32_t* wB;             // [npairs][kw] undelete(B, i) word of every position i of B
+    int kw;                   // row stride of wA / wB in words: >= k + 3, multiple of 4
+    int lG;                   // block pairs per sortlist CTA
+    int bpw;                  // blocks per warp tile (kTileElems / k)
+    uint64_t kmagic, bmagic;  // ceil(2^32 / k), ceil(2^32 / bpw): exact division of tile indices
     int64_t start[4];         // batched launches: this signal's first item per kernel
 };
 
@@ -50,6 +57,15 @@ struct UnwindPlan {
     int nw, ns;               // bitset words; summary words (0: one summary word in a register)
     uint32_t words_per_warp;
     int64_t items;            // warp groups in the launch
+};
+// Fused path: one kernel sorts the blocks (warp merge sort of 1024-element
+// tiles), merges the pairs and makes B's unwind links; the chain kernel reads
+// its list words.  Packed chain format only (slots fit in 10 bits).
+constexpr int kFusedMaxK = 1021;
+constexpr int kTileElems = 1024;                 // elements per warp tile
+constexpr int kSortListWarps = 8;
+struct ListPlan {
+    int warps;                // warps per CTA (tiles)
 };
 struct ChainPlan {
     bool packed;              // one 32-bit word per list node (k <= 1021)
@@ -83,6 +99,9 @@ struct Elem {
 };
 
 int pipeline_max_k(bool wide = false);
+size_t sortlist_smem_bytes(int warps);
+cudaError_t sortlist_setup();
+cudaError_t launch_sortlist(const SegTable& tab, int64_t items, int warps, cudaStream_t stream);
 size_t pipeline_workspace_bytes(int64_t n, int k);
 cudaError_t pipeline_setup();
 // rank: 0-based order statistic printed for every window (the median of an

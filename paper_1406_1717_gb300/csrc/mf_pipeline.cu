@@ -37,30 +37,6 @@ namespace mf {
 
 
 // ===========================================================================
-// Signals and work items.  Every kernel works on items (sortmerge and
-// epilogue: CTAs of G consecutive block pairs; unwind: warp groups of blocks;
-// chain: block pairs).  A launch covers one signal (descriptor passed by
-// value) or a batch of signals (device table; each descriptor carries the
-// index of its first item in every kernel, and an item finds its signal by
-// binary search).
-// ===========================================================================
-enum { kItemSort = 0, kItemUnwind = 1, kItemChain = 2, kItemEpilogue = 3 };
-
-__device__ __forceinline__ PipeParams find_signal(const SegTable& t, int kern, int64_t item,
-                                                  int64_t* local)
-{
-    if (t.segs == nullptr) { *local = item; return t.one; }
-    int lo = 0, hi = t.nseg - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (t.segs[mid].start[kern] <= item) lo = mid; else hi = mid - 1;
-    }
-    const PipeParams p = t.segs[lo];
-    *local = item - p.start[kern];
-    return p;
-}
-
-// ===========================================================================
 // sortmerge_kernel
 // ===========================================================================
 // KeyT: uint32_t for 4-byte elements, uint64_t for 8-byte elements.
@@ -357,11 +333,13 @@ struct PairState {
 // One step i of the post-processing (Section 6.2), branch-free: delete(A, i),
 // undelete(B, i), advance if s_A + s_B < h, return the printed node
 // (isB << 15 | slot).  wa is slot i's current word (loaded after the previous
-// step's last store); the next step's word is loaded into *wnext.
+// step's last store); the next step's word is loaded into *wnext.  B's
+// position i comes back with the links pb / nb that unwind(B) left it and
+// joint rank rb; wbw is its list word make(pb, nb, rb).
 template <bool PACKED>
 __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>& L, uint32_t i,
                                               uint32_t wa, uint32_t pb, uint32_t nb, uint32_t rb,
-                                              int h, uint32_t* wnext)
+                                              uint32_t wbw, int h, uint32_t* wnext)
 {
     using LL = Lists<PACKED>;
     // -------- delete(A, i) ----------------------------------------------------
@@ -387,7 +365,7 @@ __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>
     if (PACKED) st.rmA = st.wmA >> 20; else st.rmA = chgA ? rtA : st.rmA;
     st.sA -= (small || sApos) ? 1 : 0;                  // s <- max(0, s - 1)
     // -------- undelete(B, i) ----------------------------------------------------
-    L.st(i, LL::make(pb, nb, rb));
+    L.st(i, wbw);                                       // wbw = make(pb, nb, rb)
     if (!PACKED) L.JR(i) = (uint16_t)rb;
     L.set_next(pb, i, nb);                              // next[prev[i]] <- i
     L.set_prev(nb, i, pb);                              // prev[next[i]] <- i
@@ -501,8 +479,9 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
             if (i < NB) {
                 const uint32_t rb = t & 1 ? jw[t >> 1] >> 16 : jw[t >> 1] & 0xffffu;
                 uint32_t wn;
-                const uint32_t o = pair_step<PACKED>(st, L, (uint32_t)i, wa, wbv[t] >> 16,
-                                                     wbv[t] & 0xffffu, rb, h, &wn);
+                const uint32_t pb = wbv[t] >> 16, nb = wbv[t] & 0xffffu;
+                const uint32_t o = pair_step<PACKED>(st, L, (uint32_t)i, wa, pb, nb, rb,
+                                                     LL::make(pb, nb, rb), h, &wn);
                 wa = wn;
                 ov[t >> 1] |= (t & 1) ? (o << 16) : o;
             }
@@ -513,7 +492,74 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
     }
 }
 
-template <bool PACKED>
+// Fused path (sortlist_kernel wrote the words): construct(A) is a copy of the
+// pair's row of list words (slots 0..k+1, m_A in slot k+2); step i undeletes
+// B's position i with the word wB[i] = make(pb, nb, rb).  Packed format only.
+__device__ __forceinline__ void chain_body_words(const PipeParams& p, uint32_t* wsl, int lane,
+                                                 int64_t q, uint32_t NL)
+{
+    using LL = Lists<true>;
+    const int k = p.k, h = p.h;
+    const int NB = (int)min((int64_t)k, p.n - (q + 1) * (int64_t)k);
+    LL L;
+    L.w = wsl + lane;
+    L.jr16 = nullptr;
+    L.NL = NL;
+    const uint4* wa4 = reinterpret_cast<const uint4*>(p.wA + (size_t)q * p.kw);
+    const int nrec = (k + 2 + 3) >> 2;
+#pragma unroll 4
+    for (int c = 0; c < nrec; ++c) {
+        const uint4 v = __ldg(wa4 + c);
+        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (4 * c + t < k + 2) L.st(4 * c + t, vv[t]);
+    }
+    PairState st;
+    st.mA = __ldg(p.wA + (size_t)q * p.kw + k + 2);
+    st.wmA = L.ld(st.mA);
+    st.rmA = st.wmA >> 20;
+    st.sA = h;
+    st.mB = (uint32_t)k + 1;
+    st.wmB = L.ld(st.mB);
+    st.rmB = LL::RINF;
+    st.sB = 0;
+
+    // ---- the k steps, 8 at a time; B words of the next two chunks in flight ---
+    const uint4* wb4 = reinterpret_cast<const uint4*>(p.wB + (size_t)q * p.kw);
+    uint4* out4 = reinterpret_cast<uint4*>(p.out + (size_t)q * p.kp);
+    const int nch = (NB + 7) >> 3;
+    uint4 u0 = __ldg(wb4), u1 = __ldg(wb4 + 1);
+    uint4 v0 = u0, v1 = u1;
+    if (nch > 1) { v0 = __ldg(wb4 + 2); v1 = __ldg(wb4 + 3); }
+    uint32_t wa = L.ld(0);
+    for (int c = 0; c < nch; ++c) {
+        uint4 x0 = v0, x1 = v1;
+        if (c + 2 < nch) {
+            x0 = __ldg(wb4 + 2 * (c + 2));
+            x1 = __ldg(wb4 + 2 * (c + 2) + 1);
+        }
+        const uint32_t wbv[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+        uint32_t ov[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int i = 8 * c + t;
+            if (i < NB) {
+                const uint32_t w = wbv[t];
+                uint32_t wn;
+                const uint32_t o = pair_step<true>(st, L, (uint32_t)i, wa, LL::prv(w), LL::nxt(w),
+                                                   w >> 20, w, h, &wn);
+                wa = wn;
+                ov[t >> 1] |= (t & 1) ? (o << 16) : o;
+            }
+        }
+        out4[c] = make_uint4(ov[0], ov[1], ov[2], ov[3]);
+        u0 = v0; u1 = v1;
+        v0 = x0; v1 = x1;
+    }
+}
+
+template <bool PACKED, bool WORDS>
 __global__ void __launch_bounds__(kPipeThreads)
 chain_kernel(SegTable tab, ChainPlan cp)
 {
@@ -531,7 +577,8 @@ chain_kernel(SegTable tab, ChainPlan cp)
     int64_t q;                                          // pair j = q + 1 of its signal
     const PipeParams p = find_signal(tab, kItemChain, item, &q);
     uint32_t* wsl = reinterpret_cast<uint32_t*>(smem) + (uint32_t)pair_off * cp.lane_words;
-    chain_body<PACKED>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL);
+    if (WORDS) chain_body_words(p, wsl, lane, q, (uint32_t)NL);
+    else chain_body<PACKED>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL);
 }
 
 // ===========================================================================
@@ -585,7 +632,7 @@ epilogue_kernel(SegTable tab, int G)
         }
     }
     if (j0 == 1 && threadIdx.x == 0) {
-        const int pm = p.perm[p.h];
+        const int pm = p.wA ? (int)p.wA[k + 2] : (int)p.perm[p.h];     // P_0[h]
         reinterpret_cast<ValT*>(p.y)[0] = xs[pm];
         if (p.argmed) p.argmed[0] = pm;
     }
@@ -666,26 +713,41 @@ int pipeline_max_k(bool wide)
 
 // scratch of one signal: perm, rank, sorted-order links, unwind links per
 // block; joint ranks of A and B and printed nodes per pair
+// (four-kernel path); the fused path's rows of list words (wA, wB) and
+// printed nodes need less, so one size serves both
 static uint64_t signal_scratch_bytes(int64_t n, int k)
 {
     const int64_t nblocks = (n + k - 1) / k;
     const int64_t npairs = nblocks - 1;
     const uint64_t kp = (uint64_t)((k + 7) & ~7);
+    const uint64_t kw = (uint64_t)((k + 3 + 7) & ~7);
     const uint64_t np1 = (uint64_t)(npairs > 0 ? npairs : 1);
-    return al256(2ull * nblocks * kp) * 2 + al256(4ull * nblocks * kp) * 2 + al256(2ull * np1 * kp) * 3;
+    const uint64_t four = al256(2ull * nblocks * kp) * 2 + al256(4ull * nblocks * kp) * 2 +
+                          al256(2ull * np1 * kp) * 3;
+    const uint64_t fused = al256(4ull * np1 * kw) * 2 + al256(2ull * np1 * kp);
+    return four > fused ? four : fused;
 }
 
-static void carve_signal(PipeParams& p, char*& w)
+static void carve_signal(PipeParams& p, char*& w, bool fused)
 {
     const uint64_t kp = (uint64_t)p.kp;
     const uint64_t np1 = (uint64_t)(p.npairs > 0 ? p.npairs : 1);
-    p.perm = (uint16_t*)w;  w += al256(2ull * p.nblocks * kp);
-    p.rnk = (uint16_t*)w;   w += al256(2ull * p.nblocks * kp);
-    p.slink = (uint32_t*)w; w += al256(4ull * p.nblocks * kp);
-    p.ulink = (uint32_t*)w; w += al256(4ull * p.nblocks * kp);
-    p.ja = (uint16_t*)w;    w += al256(2ull * np1 * kp);
-    p.jb = (uint16_t*)w;    w += al256(2ull * np1 * kp);
-    p.out = (uint16_t*)w;   w += al256(2ull * np1 * kp);
+    char* const w0 = w;
+    if (fused) {
+        p.kw = (p.k + 3 + 7) & ~7;
+        p.wA = (uint32_t*)w;    w += al256(4ull * np1 * (uint64_t)p.kw);
+        p.wB = (uint32_t*)w;    w += al256(4ull * np1 * (uint64_t)p.kw);
+        p.out = (uint16_t*)w;
+    } else {
+        p.perm = (uint16_t*)w;  w += al256(2ull * p.nblocks * kp);
+        p.rnk = (uint16_t*)w;   w += al256(2ull * p.nblocks * kp);
+        p.slink = (uint32_t*)w; w += al256(4ull * p.nblocks * kp);
+        p.ulink = (uint32_t*)w; w += al256(4ull * p.nblocks * kp);
+        p.ja = (uint16_t*)w;    w += al256(2ull * np1 * kp);
+        p.jb = (uint16_t*)w;    w += al256(2ull * np1 * kp);
+        p.out = (uint16_t*)w;
+    }
+    w = w0 + signal_scratch_bytes(p.n, p.k);
 }
 
 static void fill_signal(PipeParams& p, const void* x, void* y, int32_t* argmed,
@@ -720,8 +782,10 @@ cudaError_t pipeline_setup()
     if ((e = cudaFuncSetAttribute(epilogue_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
     if ((e = cudaFuncSetAttribute(unwind_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
     if ((e = cudaFuncSetAttribute(unwind_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
-    if ((e = cudaFuncSetAttribute(chain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
-    if ((e = cudaFuncSetAttribute(chain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(chain_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(chain_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(chain_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = sortlist_setup())) return e;
     return cudaFuncSetAttribute(epilogue_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
 }
 
@@ -732,6 +796,9 @@ cudaError_t pipeline_setup()
 struct ClassPlan {
     int kmax;
     bool wide;                // 8-byte elements
+    bool fused;               // sortlist + chain (words) + epilogue
+    int lwarps;               // fused: warps (tiles) per sortlist CTA
+    int lGcap;                // fused: cap on block pairs per sortlist CTA
     SortPlan sp;  size_t sbytes;
     UnwindPlan up; size_t ubytes; int uwarps; int bpw;
     ChainPlan cp; size_t cbytes;
@@ -764,10 +831,16 @@ static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tu
     if (Gcap == 0) return false;
     const int cls = tune_class_of(kmax);
     if (tune) tune += cls;
+    const int64_t want = (total_pairs + 2ll * num_sms - 1) / (2ll * num_sms);
+    // fused path: 4-byte elements whose lists fit the packed chain format
+    c->fused = !wide && kmax <= kFusedMaxK;
+    c->lwarps = kSortListWarps;
+    c->lGcap = 1 << 30;
+    if (tune && tune->sort_G > 0) c->lGcap = tune->sort_G;
+    if (want >= 1 && want < c->lGcap) c->lGcap = (int)want;
     int G = Gcap;
     if (kBuiltinSortG[cls] > 0) G = min(G, kBuiltinSortG[cls]);
     if (tune && tune->sort_G > 0) G = min(Gcap, tune->sort_G);
-    const int64_t want = (total_pairs + 2ll * num_sms - 1) / (2ll * num_sms);
     if (want >= 1 && want < G) G = (int)want;
     sort_plan(kmax, G, &c->sp, &c->sbytes, wide);
     c->sp.G = G;
@@ -798,10 +871,18 @@ static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tu
 static void count_items(PipeParams& p, const ClassPlan& c, int64_t* tot)
 {
     const int64_t np = p.npairs;
-    const int64_t cnt[4] = {np > 0 ? (np + c.sp.G - 1) / c.sp.G : 1,
-                            np > 0 ? (np + c.bpw - 1) / c.bpw : 0,
-                            np,
-                            np > 0 ? (np + c.GE - 1) / c.GE : 1};
+    int64_t cnt[4] = {np > 0 ? (np + c.sp.G - 1) / c.sp.G : 1,
+                      np > 0 ? (np + c.bpw - 1) / c.bpw : 0,
+                      np,
+                      np > 0 ? (np + c.GE - 1) / c.GE : 1};
+    if (c.fused) {
+        p.bpw = kTileElems / p.k;
+        p.lG = max(1, min(c.lwarps * p.bpw - 1, c.lGcap));
+        p.kmagic = ((1ull << 32) + (uint64_t)p.k - 1) / (uint64_t)p.k;
+        p.bmagic = ((1ull << 32) + (uint64_t)p.bpw - 1) / (uint64_t)p.bpw;
+        cnt[0] = np > 0 ? (np + p.lG - 1) / p.lG : 1;
+        cnt[1] = 0;
+    }
     for (int i = 0; i < 4; ++i) { p.start[i] = tot[i]; tot[i] += cnt[i]; }
 }
 
@@ -819,6 +900,12 @@ static cudaError_t launch_classes(const ClassPlan* cls, const SegTable* tabs, co
     cudaError_t e;
     TIMER_MARK(0);
     for (int c = 0; c < ncls; ++c) {
+        if (cls[c].fused) {
+            if ((e = launch_sortlist(tabs[c], tot[c][kItemSort], cls[c].lwarps, stream)) != cudaSuccess)
+                return e;
+            if (stats) stats->launches += 1;
+            continue;
+        }
         if (cls[c].wide)
             sortmerge_kernel<uint64_t><<<(unsigned)tot[c][kItemSort], kPipeThreads, cls[c].sbytes, stream>>>(tabs[c], cls[c].sp);
         else
@@ -845,10 +932,12 @@ static cudaError_t launch_classes(const ClassPlan* cls, const SegTable* tabs, co
         ChainPlan cp = cls[c].cp;
         cp.items = tot[c][kItemChain];
         const int64_t grid = (cp.items + cp.pairs_per_cta - 1) / cp.pairs_per_cta;
-        if (cp.packed)
-            chain_kernel<true><<<(unsigned)grid, 32 * cp.nwarps, cls[c].cbytes, stream>>>(tabs[c], cp);
+        if (cls[c].fused)
+            chain_kernel<true, true><<<(unsigned)grid, 32 * cp.nwarps, cls[c].cbytes, stream>>>(tabs[c], cp);
+        else if (cp.packed)
+            chain_kernel<true, false><<<(unsigned)grid, 32 * cp.nwarps, cls[c].cbytes, stream>>>(tabs[c], cp);
         else
-            chain_kernel<false><<<(unsigned)grid, 32 * cp.nwarps, cls[c].cbytes, stream>>>(tabs[c], cp);
+            chain_kernel<false, false><<<(unsigned)grid, 32 * cp.nwarps, cls[c].cbytes, stream>>>(tabs[c], cp);
         if (stats) stats->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -876,11 +965,11 @@ cudaError_t launch_pipeline(const void* x, int64_t n, int k, int rank, Elem el,
     tab.segs = nullptr;
     tab.nseg = 1;
     fill_signal(tab.one, x, y, argmed, n, k, rank, el.is_float);
-    char* w = (char*)ws;
-    carve_signal(tab.one, w);
     ClassPlan cls;
     if (!make_class_plan(k, tab.one.npairs, num_sms, stats ? stats->tune : nullptr, el.wide, &cls))
         return cudaErrorInvalidValue;
+    char* w = (char*)ws;
+    carve_signal(tab.one, w, cls.fused);
     int64_t tot[1][4] = {{0, 0, 0, 0}};
     count_items(tab.one, cls, tot[0]);
     return launch_classes(&cls, &tab, tot, 1, stream, stats);
@@ -947,7 +1036,7 @@ cudaError_t launch_pipeline_batched(const void* x, void* y, int32_t* argmed, Ele
         const int eb = el.bytes();
         fill_signal(p, (const char*)x + x_off[s] * eb, (char*)y + y_off[s] * eb,
                     argmed ? argmed + y_off[s] : nullptr, n[s], k[s], (k[s] - 1) / 2, el.is_float);
-        carve_signal(p, w);
+        carve_signal(p, w, plans[cls_index[c]].fused);
         count_items(p, plans[cls_index[c]], tot[cls_index[c]]);
     }
     for (int c = 0; c < kNumClasses; ++c) {

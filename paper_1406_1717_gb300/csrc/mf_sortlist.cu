@@ -1,0 +1,364 @@
+// mf_sortlist.cu -- the fused front half of the pipeline for 4-byte elements
+// and k <= kFusedMaxK: piecewise sort, joint ranks, unwind links and the list
+// words of both block data structures of every pair, in one kernel.
+//
+// Paper: "Median Filtering is Equivalent to Sorting" (Suomela).
+//   * stable block sort ........ Section 3 "Piecewise Sorting", Section 5.2:
+//                                sorting the pairs (alpha[i], i) in
+//                                lexicographic order gives a stable pi
+//   * construct(A) ............. Section 5.3 (Fig. block-impl): A's list in
+//                                sorted order through the sentinel k
+//   * unwind(B) ................ Section 4 "Unwind": delete(k-1), ..., delete(0)
+//                                leaves in position i the prev / next that i's
+//                                list had when i was deleted, i.e. the nearest
+//                                smaller / larger element among positions < i
+//   * joint ranks .............. comparisons (alpha[i], i) < (alpha[m], m) of
+//                                Section 5.3 and peek(A) <= peek(B) of Section
+//                                6.2 as comparisons of ranks in the merged
+//                                order of the pair (A first on equal keys)
+//
+// One CTA covers G consecutive block pairs, i.e. G + 1 blocks.  Each warp owns
+// a tile of up to 1024 elements: bpw = 1024 / k whole blocks.  Elements become
+// 64-bit composites (block in tile : 32-bit order key : position in block),
+// all distinct, so plain ascending order of composites is the stable sort of
+// every block of the tile at once:
+//   1. every lane sorts 32 composites in registers (Batcher's odd-even merge
+//      sorting network, 191 compare-exchanges);
+//   2. five merge-path rounds in shared memory merge the 32 runs to one;
+//   3. per pair, lanes merge A's and B's sorted runs by key (A first on ties)
+//      and record each element's joint rank;
+//   4. per block of the tile: perm / rank in place of the tile; as A, the list
+//      words next | prev << 10 | joint rank << 20 of construct(A) (plus the
+//      sentinel words and m_A = pi[h]); as B, the unwind links from prefix
+//      bitsets of ranks (32 lanes, each a run of consecutive positions seeded
+//      with the ranks of all positions before it) and the undelete words.
+// Shared memory per warp: the padded tile (8448 bytes; element x at x + x/32
+// so the lane-major stores of step 1 and the merge write-backs are free of
+// bank conflicts), plus 4 KB per warp of joint-rank rows.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "mf_device.cuh"
+#include "mf_internal.h"
+
+namespace mf {
+
+namespace {
+
+constexpr int kTileU64 = kTileElems + kTileElems / 32;    // padded tile in 8-byte words
+constexpr uint32_t kTileBytes = kTileU64 * 8;
+constexpr uint64_t kPadComp = ~0ull;                       // above every composite
+constexpr uint32_t kRankInf = 0x7ffu;                      // sentinel rank (11 bits)
+
+__device__ __forceinline__ int tix(int x) { return x + (x >> 5); }
+
+__host__ __device__ __forceinline__ void cmpx(uint64_t& a, uint64_t& b)
+{
+    const bool sw = b < a;
+    const uint64_t lo = sw ? b : a, hi = sw ? a : b;
+    a = lo;
+    b = hi;
+}
+
+// Batcher's odd-even merge sort (Batcher 1968) on v[LO..HI] (inclusive),
+// unrolled at compile time: sort both halves, then odd-even merge.
+template <int LO, int HI, int R>
+struct OddEvenMerge {
+    __host__ __device__ __forceinline__ static void run(uint64_t (&v)[32])
+    {
+        if constexpr (2 * R < HI - LO) {
+            OddEvenMerge<LO, HI, 2 * R>::run(v);
+            OddEvenMerge<LO + R, HI, 2 * R>::run(v);
+#pragma unroll
+            for (int i = LO + R; i < HI - R; i += 2 * R) cmpx(v[i], v[i + R]);
+        } else {
+            cmpx(v[LO], v[LO + R]);
+        }
+    }
+};
+template <int LO, int HI>
+struct OddEvenSort {
+    __host__ __device__ __forceinline__ static void run(uint64_t (&v)[32])
+    {
+        if constexpr (HI - LO >= 1) {
+            constexpr int MID = LO + (HI - LO) / 2;
+            OddEvenSort<LO, MID>::run(v);
+            OddEvenSort<MID + 1, HI>::run(v);
+            OddEvenMerge<LO, HI, 1>::run(v);
+        }
+    }
+};
+
+// Sort the warp's tile.  On entry lane L holds 32 composites in v (any
+// order); on exit T holds all 1024 in ascending order (padded layout) and v
+// is clobbered.
+__device__ __forceinline__ void tile_sort(uint64_t* T, uint64_t (&v)[32], int lane)
+{
+    OddEvenSort<0, 31>::run(v);
+    const int o0 = 32 * lane;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) T[tix(o0 + i)] = v[i];
+    __syncwarp();
+#pragma unroll 1
+    for (int R = 32; R < kTileElems; R <<= 1) {
+        // runs [B0, B0 + R) and [B0 + R, B0 + 2R); this lane's outputs are
+        // merged positions d .. d + 31 of that pair of runs
+        const int B0 = o0 & ~(2 * R - 1);
+        const int d = o0 - B0;
+        int lo = max(0, d - R), hi = min(d, R);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (T[tix(B0 + mid)] < T[tix(B0 + R + d - 1 - mid)]) lo = mid + 1; else hi = mid;
+        }
+        int a = lo, b = d - lo;
+        uint64_t ha = a < R ? T[tix(B0 + a)] : kPadComp;
+        uint64_t hb = b < R ? T[tix(B0 + R + b)] : kPadComp;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const bool ta = ha < hb;
+            v[i] = ta ? ha : hb;
+            a += ta ? 1 : 0;
+            b += ta ? 0 : 1;
+            const int nx = ta ? a : b;
+            const int src = (ta ? B0 : B0 + R) + nx;
+            uint64_t nv = kPadComp;
+            if (nx < R) nv = T[tix(src)];
+            ha = ta ? nv : ha;
+            hb = ta ? hb : nv;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) T[tix(o0 + i)] = v[i];
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ uint32_t comp_key(uint64_t c) { return (uint32_t)(c >> 10); }
+__device__ __forceinline__ uint32_t comp_pos(uint64_t c) { return (uint32_t)c & 1023u; }
+__device__ __forceinline__ uint32_t udiv(uint32_t x, uint64_t magic)
+{
+    return (uint32_t)(((uint64_t)x * magic) >> 32);
+}
+
+__global__ void __launch_bounds__(kSortListWarps * 32, 2)
+sortlist_kernel(SegTable tab)
+{
+    int64_t cta;
+    const PipeParams p = find_signal(tab, kItemSort, blockIdx.x, &cta);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int W = blockDim.x >> 5;
+    const int k = p.k, bpw = p.bpw, G = p.lG;
+    const int64_t j0 = 1 + cta * G;                     // first pair of this CTA
+    const int64_t left = p.npairs - (j0 - 1);
+    const int npair = (int)(left < G ? (left > 0 ? left : 0) : G);
+    const int nblk = npair + 1;
+    const int64_t ebase = (j0 - 1) * (int64_t)k;
+    const int64_t rem = p.n - ebase;
+    const int E = (int)((int64_t)nblk * k < rem ? (int64_t)nblk * k : rem);
+    uint64_t* tiles = reinterpret_cast<uint64_t*>(smem);
+    uint16_t* jaS = reinterpret_cast<uint16_t*>(smem + (size_t)W * kTileBytes);
+    uint16_t* jbS = jaS + (size_t)G * k;
+    uint64_t* T = tiles + (size_t)warp * kTileU64;
+    const int tile_e0 = warp * bpw * k;
+    const int tile_n = max(0, min(bpw * k, E - tile_e0));
+
+    // ---- 1. keys of the CTA's span (coalesced), then 32 composites per lane ----
+    uint32_t* keys = reinterpret_cast<uint32_t*>(smem);
+    const uint32_t* xp = reinterpret_cast<const uint32_t*>(p.x) + ebase;
+    for (int e = tid; e < E; e += blockDim.x) keys[e] = to_key(__ldg(xp + e), p.is_float);
+    __syncthreads();
+    uint64_t v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int et = 32 * lane + ((i + lane) & 31);   // rotated: conflict-free reads
+        uint64_t c = kPadComp;
+        if (et < tile_n) {
+            const uint32_t blk = udiv((uint32_t)et, p.kmagic);
+            const uint32_t pos = (uint32_t)et - blk * (uint32_t)k;
+            c = ((uint64_t)blk << 42) | ((uint64_t)keys[tile_e0 + et] << 10) | pos;
+        }
+        v[i] = c;
+    }
+    __syncthreads();                                    // keys read before tiles are written
+    // ---- 2. warp merge sort of the tile ------------------------------------------
+    if (tile_n > 0) tile_sort(T, v, lane);
+    __syncthreads();
+
+    // ---- 3. joint ranks of every pair: merge A's and B's runs, A first on ties ---
+    {
+        int lpp = 1;                                    // lanes per pair, about 64 outputs each
+        while (lpp < 32 && lpp * 64 < 2 * k) lpp <<= 1;
+        const int ppw = 32 / lpp;
+        const int sub = lane & (lpp - 1);
+        for (int g0 = warp * ppw; g0 < npair; g0 += W * ppw) {
+            const int g = g0 + lane / lpp;
+            if (g >= npair) continue;
+            const int NB = min(k, E - (g + 1) * k);
+            const int tot = k + NB;
+            const int chunk = (tot + lpp - 1) / lpp;
+            const int o0 = min(sub * chunk, tot), o1 = min(o0 + chunk, tot);
+            const int tA = (int)udiv((uint32_t)g, p.bmagic), tB = (int)udiv((uint32_t)(g + 1), p.bmagic);
+            const uint64_t* TA = tiles + (size_t)tA * kTileU64;
+            const uint64_t* TB = tiles + (size_t)tB * kTileU64;
+            const int offA = (g - tA * bpw) * k, offB = (g + 1 - tB * bpw) * k;
+            int lo = max(0, o0 - NB), hi = min(o0, k);
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (comp_key(TA[tix(offA + mid)]) <= comp_key(TB[tix(offB + o0 - 1 - mid)])) lo = mid + 1;
+                else hi = mid;
+            }
+            int ia = lo, ib = o0 - lo;
+            uint64_t ca = ia < k ? TA[tix(offA + ia)] : 0ull;
+            uint64_t cb = ib < NB ? TB[tix(offB + ib)] : 0ull;
+            uint16_t* ja = jaS + (size_t)g * k;
+            uint16_t* jb = jbS + (size_t)g * k;
+            for (int o = o0; o < o1; ++o) {
+                const bool ta = ib >= NB || (ia < k && comp_key(ca) <= comp_key(cb));
+                if (ta) {
+                    ja[comp_pos(ca)] = (uint16_t)o;
+                    if (++ia < k) ca = TA[tix(offA + ia)];
+                } else {
+                    jb[comp_pos(cb)] = (uint16_t)o;
+                    if (++ib < NB) cb = TB[tix(offB + ib)];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tile_n == 0) return;
+
+    // ---- 4. per block of the tile ------------------------------------------------
+    // The tile becomes: perm (u16, by sorted index), rank (u16, by block
+    // position) and a 4352-byte area for bitsets, then unwind links.
+    uint16_t* permW = reinterpret_cast<uint16_t*>(T);
+    uint16_t* rnkW = permW + kTileElems;
+    uint32_t* areaW = reinterpret_cast<uint32_t*>(rnkW + kTileElems);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = T[tix(lane + 32 * i)];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int x = lane + 32 * i;
+        if (x < tile_n) {
+            const uint32_t pos = comp_pos(v[i]);
+            const uint32_t blk = (uint32_t)(v[i] >> 42);
+            permW[x] = (uint16_t)pos;
+            rnkW[blk * k + pos] = (uint16_t)(x - blk * k);
+        }
+    }
+    __syncwarp();
+
+    const int nbt = (tile_n + k - 1) / k;
+    for (int bt = 0; bt < nbt; ++bt) {
+        const int b = warp * bpw + bt;                  // block of the CTA
+        const int boff = bt * k;
+        const int len = min(k, tile_n - boff);
+        const uint16_t* pm = permW + boff;
+        const uint16_t* rk = rnkW + boff;
+        // -- as A of pair b: construct(A) in slot space (Section 5.3) -------------
+        if (b < npair) {
+            uint32_t* wa = p.wA + (size_t)(j0 - 1 + b) * p.kw;
+            const uint16_t* ja = jaS + (size_t)b * k;
+            for (int pos = lane; pos < k; pos += 32) {
+                const int t = rk[pos];
+                const uint32_t pv = t > 0 ? pm[t - 1] : (uint32_t)k;
+                const uint32_t nx = t + 1 < k ? pm[t + 1] : (uint32_t)k;
+                wa[pos] = nx | (pv << 10) | ((uint32_t)ja[pos] << 20);
+            }
+            if (lane == 0) {
+                wa[k] = (uint32_t)pm[0] | ((uint32_t)pm[k - 1] << 10) | (kRankInf << 20);
+                wa[k + 1] = (uint32_t)(k + 1) | ((uint32_t)(k + 1) << 10) | (kRankInf << 20);
+                wa[k + 2] = pm[p.h];
+            }
+        } else if (npair == 0 && lane == 0) {
+            p.wA[k + 2] = pm[p.h];                      // one block only: y[0] = X_0[P_0[h]]
+        }
+        // -- as B of pair b - 1: unwind links (Section 4), undelete words --------
+        if (b >= 1) {
+            const int NB = len;
+            const int cs = (NB + 31) >> 5;             // positions per lane (a run)
+            const int nw = cs;                          // bitset words for ranks < NB
+            const int p0 = min(lane * cs, NB), p1 = min(p0 + cs, NB);
+            uint32_t* bw = areaW + lane;                // word w of this lane at bw[32 w]
+            for (int w = 0; w < nw; ++w) bw[32 * w] = 0u;
+            for (int pos = p0; pos < p1; ++pos) {
+                const int r = rk[pos];
+                bw[32 * (r >> 5)] |= 1u << (r & 31);
+            }
+            // exclusive OR-scan over lanes: the ranks of all positions before p0
+            uint32_t summ = 0;                          // bit w: word w non-empty
+            for (int w = 0; w < nw; ++w) {
+                uint32_t x = bw[32 * w];
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, x, off);
+                    if (lane >= off) x |= y;
+                }
+                uint32_t ex = __shfl_up_sync(kFull, x, 1);
+                if (lane == 0) ex = 0u;
+                bw[32 * w] = ex;
+                summ |= ex ? (1u << w) : 0u;
+            }
+            // the run: predecessor / successor of rank(pos) among earlier positions
+            uint32_t uo[32];
+            const uint32_t sentB = (uint32_t)k + 1;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                uo[i] = 0u;
+                const int pos = p0 + i;
+                if (pos < p1) {
+                    const int r = rk[pos];
+                    const int w = r >> 5, bb = r & 31;
+                    const uint32_t word = bw[32 * w];
+                    const uint32_t mlo = word & ((1u << bb) - 1u);
+                    const uint32_t mhi = word & ~((2u << bb) - 1u);    // bb = 31: 0
+                    const uint32_t slo = summ & ((1u << w) - 1u);
+                    const uint32_t shi = summ & ~((2u << w) - 1u);
+                    const int wlo = slo ? 31 - __clz(slo) : 0;
+                    const int whi = shi ? __ffs(shi) - 1 : 0;
+                    const uint32_t xlo = bw[32 * wlo], xhi = bw[32 * whi];
+                    const int pred = mlo ? ((w << 5) | (31 - __clz(mlo)))
+                                         : (slo ? ((wlo << 5) | (31 - __clz(xlo))) : -1);
+                    const int succ = mhi ? ((w << 5) | (__ffs(mhi) - 1))
+                                         : (shi ? ((whi << 5) | (__ffs(xhi) - 1)) : -1);
+                    bw[32 * w] = word | (1u << bb);
+                    summ |= 1u << w;
+                    const uint32_t pv = pred >= 0 ? (uint32_t)pm[pred] : sentB;
+                    const uint32_t nx = succ >= 0 ? (uint32_t)pm[succ] : sentB;
+                    uo[i] = nx | (pv << 10);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (p0 + i < p1) areaW[tix(p0 + i)] = uo[i];
+            __syncwarp();
+            uint32_t* wb = p.wB + (size_t)(j0 - 1 + b - 1) * p.kw;
+            const uint16_t* jb = jbS + (size_t)(b - 1) * k;
+            for (int pos = lane; pos < NB; pos += 32)
+                wb[pos] = areaW[tix(pos)] | ((uint32_t)jb[pos] << 20);
+            __syncwarp();
+        }
+    }
+}
+
+}  // namespace
+
+size_t sortlist_smem_bytes(int warps)
+{
+    return (size_t)warps * (kTileBytes + 4u * kTileElems);
+}
+
+cudaError_t sortlist_setup()
+{
+    return cudaFuncSetAttribute(sortlist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sortlist_smem_bytes(kSortListWarps));
+}
+
+cudaError_t launch_sortlist(const SegTable& tab, int64_t items, int warps, cudaStream_t stream)
+{
+    sortlist_kernel<<<(unsigned)items, 32 * warps, sortlist_smem_bytes(warps), stream>>>(tab);
+    return cudaGetLastError();
+}
+
+}  // namespace mf

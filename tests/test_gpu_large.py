@@ -186,7 +186,10 @@ def test_tiers_agree_and_threshold_resets(handle, large_handle):
         mf.mf_set_tier_threshold(h, 0)
         l0 = mf.mf_launch_count(h)
         gpu_filter(h, x, 1001)
-        assert mf.mf_launch_count(h) - l0 == 4          # the four pipeline kernels
+        assert mf.mf_launch_count(h) - l0 == 3          # fused sort, chains, store
+        l0 = mf.mf_launch_count(h)
+        gpu_filter(h, x, 2047)
+        assert mf.mf_launch_count(h) - l0 == 4          # the four-kernel pipeline
         l0 = mf.mf_launch_count(h)
         gpu_filter(h, x, 6001)                           # default crossover: large-k tier
         assert mf.mf_launch_count(h) - l0 > 4
