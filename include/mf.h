@@ -237,14 +237,18 @@ mf_status mf_get_tier_threshold(mf_handle h, int32_t* k_large_from);
 
 /* Per-kernel timing for measurement.  With timing enabled, every mf_filter /
  * mf_filter_host call records CUDA events on the handle's stream around its
- * four kernel groups (sort+merge, unwind, post-processing chains, store; on
- * the large-k tier: chunk sort, merge tiers and joint ranks / unwind /
- * segment states and chains / store), in a ring of the last 128 calls;
- * enabling resets the ring. */
+ * four kernel groups (sort, unwind, post-processing chains, store), in a ring
+ * of the last 128 calls; enabling resets the ring.  The groups per path:
+ *   4-byte elements, k <= 1021: the fused sort kernel (block sort, joint
+ *     ranks, unwind links, list words) / nothing / chains / store;
+ *   other windows of the shared-memory pipeline: sort + joint ranks /
+ *     unwind links / chains / store;
+ *   large-k tier: chunk sort, merge tiers and joint ranks / unwind /
+ *     segment states and chains / store. */
 mf_status mf_set_timing(mf_handle h, int enable);
 
 /* Sum of each kernel's duration (ms) over the last `ncalls` timed calls
- * (at most 128): ms[0] sort+merge, ms[1] unwind, ms[2] chains, ms[3] store.
+ * (at most 128): ms[0] sort, ms[1] unwind, ms[2] chains, ms[3] store.
  * Waits for those calls to finish. */
 mf_status mf_kernel_times(mf_handle h, int32_t ncalls, float* ms);
 

@@ -221,7 +221,7 @@ def mf_launch_count(handle) -> int:
     return int(c.value)
 
 
-KERNEL_NAMES = ("sortmerge", "unwind", "chain", "epilogue")
+KERNEL_NAMES = ("sort", "unwind", "chain", "store")
 
 
 def mf_set_tuning(handle, k: int, sort_pairs_per_cta: int = 0, store_pairs_per_cta: int = 0):

@@ -51,10 +51,11 @@ constexpr uint32_t kRankInf = 0x7ffu;                      // sentinel rank (11 
 
 __device__ __forceinline__ int tix(int x) { return x + (x >> 5); }
 
-__host__ __device__ __forceinline__ void cmpx(uint64_t& a, uint64_t& b)
+template <typename V>
+__host__ __device__ __forceinline__ void cmpx(V& a, V& b)
 {
     const bool sw = b < a;
-    const uint64_t lo = sw ? b : a, hi = sw ? a : b;
+    const V lo = sw ? b : a, hi = sw ? a : b;
     a = lo;
     b = hi;
 }
@@ -63,7 +64,8 @@ __host__ __device__ __forceinline__ void cmpx(uint64_t& a, uint64_t& b)
 // unrolled at compile time: sort both halves, then odd-even merge.
 template <int LO, int HI, int R>
 struct OddEvenMerge {
-    __host__ __device__ __forceinline__ static void run(uint64_t (&v)[32])
+    template <typename V>
+    __host__ __device__ __forceinline__ static void run(V (&v)[32])
     {
         if constexpr (2 * R < HI - LO) {
             OddEvenMerge<LO, HI, 2 * R>::run(v);
@@ -77,7 +79,8 @@ struct OddEvenMerge {
 };
 template <int LO, int HI>
 struct OddEvenSort {
-    __host__ __device__ __forceinline__ static void run(uint64_t (&v)[32])
+    template <typename V>
+    __host__ __device__ __forceinline__ static void run(V (&v)[32])
     {
         if constexpr (HI - LO >= 1) {
             constexpr int MID = LO + (HI - LO) / 2;
@@ -88,9 +91,31 @@ struct OddEvenSort {
     }
 };
 
+// One merge-path step: emit the smaller head, advance its run, load its next
+// element (runs A = T[B0 ..), B = T[B0 + R ..), both of length R).
+__device__ __forceinline__ uint64_t merge_step(const uint64_t* T, int B0, int R, uint64_t& ha,
+                                               uint64_t& hb, int& a, int& b);
+
+__device__ __forceinline__ uint64_t merge_step(const uint64_t* T, int B0, int R, uint64_t& ha,
+                                               uint64_t& hb, int& a, int& b)
+{
+    const bool ta = ha < hb;
+    const uint64_t out = ta ? ha : hb;
+    a += ta ? 1 : 0;
+    b += ta ? 0 : 1;
+    const int nx = ta ? a : b;
+    const int src = (ta ? B0 : B0 + R) + nx;
+    uint64_t nv = kPadComp;
+    if (nx < R) nv = T[tix(src)];
+    ha = ta ? nv : ha;
+    hb = ta ? hb : nv;
+    return out;
+}
+
 // Sort the warp's tile.  On entry lane L holds 32 composites in v (any
 // order); on exit T holds all 1024 in ascending order (padded layout) and v
-// is clobbered.
+// is clobbered.  Each merge round gives a lane two independent merge paths
+// (16 outputs each), so their loads overlap.
 __device__ __forceinline__ void tile_sort(uint64_t* T, uint64_t (&v)[32], int lane)
 {
     OddEvenSort<0, 31>::run(v);
@@ -101,29 +126,30 @@ __device__ __forceinline__ void tile_sort(uint64_t* T, uint64_t (&v)[32], int la
 #pragma unroll 1
     for (int R = 32; R < kTileElems; R <<= 1) {
         // runs [B0, B0 + R) and [B0 + R, B0 + 2R); this lane's outputs are
-        // merged positions d .. d + 31 of that pair of runs
+        // merged positions d0 .. d0 + 15 and d1 .. d1 + 15 of that pair of runs
         const int B0 = o0 & ~(2 * R - 1);
-        const int d = o0 - B0;
-        int lo = max(0, d - R), hi = min(d, R);
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (T[tix(B0 + mid)] < T[tix(B0 + R + d - 1 - mid)]) lo = mid + 1; else hi = mid;
+        const int d0 = o0 - B0, d1 = d0 + 16;
+        int lo0 = max(0, d0 - R), hi0 = min(d0, R);
+        int lo1 = max(0, d1 - R), hi1 = min(d1, R);
+        while (lo0 < hi0 || lo1 < hi1) {
+            if (lo0 < hi0) {
+                const int mid = (lo0 + hi0) >> 1;
+                if (T[tix(B0 + mid)] < T[tix(B0 + R + d0 - 1 - mid)]) lo0 = mid + 1; else hi0 = mid;
+            }
+            if (lo1 < hi1) {
+                const int mid = (lo1 + hi1) >> 1;
+                if (T[tix(B0 + mid)] < T[tix(B0 + R + d1 - 1 - mid)]) lo1 = mid + 1; else hi1 = mid;
+            }
         }
-        int a = lo, b = d - lo;
-        uint64_t ha = a < R ? T[tix(B0 + a)] : kPadComp;
-        uint64_t hb = b < R ? T[tix(B0 + R + b)] : kPadComp;
+        int a0 = lo0, b0 = d0 - lo0, a1 = lo1, b1 = d1 - lo1;
+        uint64_t ha0 = a0 < R ? T[tix(B0 + a0)] : kPadComp;
+        uint64_t hb0 = b0 < R ? T[tix(B0 + R + b0)] : kPadComp;
+        uint64_t ha1 = a1 < R ? T[tix(B0 + a1)] : kPadComp;
+        uint64_t hb1 = b1 < R ? T[tix(B0 + R + b1)] : kPadComp;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const bool ta = ha < hb;
-            v[i] = ta ? ha : hb;
-            a += ta ? 1 : 0;
-            b += ta ? 0 : 1;
-            const int nx = ta ? a : b;
-            const int src = (ta ? B0 : B0 + R) + nx;
-            uint64_t nv = kPadComp;
-            if (nx < R) nv = T[tix(src)];
-            ha = ta ? nv : ha;
-            hb = ta ? hb : nv;
+        for (int i = 0; i < 16; ++i) {
+            v[i] = merge_step(T, B0, R, ha0, hb0, a0, b0);
+            v[16 + i] = merge_step(T, B0, R, ha1, hb1, a1, b1);
         }
         __syncwarp();
 #pragma unroll
@@ -134,6 +160,7 @@ __device__ __forceinline__ void tile_sort(uint64_t* T, uint64_t (&v)[32], int la
 
 __device__ __forceinline__ uint32_t comp_key(uint64_t c) { return (uint32_t)(c >> 10); }
 __device__ __forceinline__ uint32_t comp_pos(uint64_t c) { return (uint32_t)c & 1023u; }
+
 __device__ __forceinline__ uint32_t udiv(uint32_t x, uint64_t magic)
 {
     return (uint32_t)(((uint64_t)x * magic) >> 32);
@@ -163,9 +190,23 @@ sortlist_kernel(SegTable tab)
     const int tile_n = max(0, min(bpw * k, E - tile_e0));
 
     // ---- 1. keys of the CTA's span (coalesced), then 32 composites per lane ----
+    // E <= 32 * blockDim.x: each thread issues its loads 16 at a time
     uint32_t* keys = reinterpret_cast<uint32_t*>(smem);
     const uint32_t* xp = reinterpret_cast<const uint32_t*>(p.x) + ebase;
-    for (int e = tid; e < E; e += blockDim.x) keys[e] = to_key(__ldg(xp + e), p.is_float);
+#pragma unroll 1
+    for (int i0 = 0; i0 < 32; i0 += 16) {
+        uint32_t raw[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = tid + (i0 + i) * (int)blockDim.x;
+            raw[i] = e < E ? __ldg(xp + e) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = tid + (i0 + i) * (int)blockDim.x;
+            if (e < E) keys[e] = to_key(raw[i], p.is_float);
+        }
+    }
     __syncthreads();
     uint64_t v[32];
 #pragma unroll
@@ -259,11 +300,22 @@ sortlist_kernel(SegTable tab)
         if (b < npair) {
             uint32_t* wa = p.wA + (size_t)(j0 - 1 + b) * p.kw;
             const uint16_t* ja = jaS + (size_t)b * k;
-            for (int pos = lane; pos < k; pos += 32) {
-                const int t = rk[pos];
-                const uint32_t pv = t > 0 ? pm[t - 1] : (uint32_t)k;
-                const uint32_t nx = t + 1 < k ? pm[t + 1] : (uint32_t)k;
-                wa[pos] = nx | (pv << 10) | ((uint32_t)ja[pos] << 20);
+            for (int pos0 = lane; pos0 < k; pos0 += 128) {          // four positions in flight
+                int t[4];
+                uint32_t jv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int pos = pos0 + 32 * u;
+                    t[u] = pos < k ? (int)rk[pos] : 0;
+                    jv[u] = pos < k ? (uint32_t)ja[pos] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int pos = pos0 + 32 * u;
+                    const uint32_t pv = t[u] > 0 ? pm[t[u] - 1] : (uint32_t)k;
+                    const uint32_t nx = t[u] + 1 < k ? pm[t[u] + 1] : (uint32_t)k;
+                    if (pos < k) wa[pos] = nx | (pv << 10) | (jv[u] << 20);
+                }
             }
             if (lane == 0) {
                 wa[k] = (uint32_t)pm[0] | ((uint32_t)pm[k - 1] << 10) | (kRankInf << 20);
@@ -274,6 +326,12 @@ sortlist_kernel(SegTable tab)
             p.wA[k + 2] = pm[p.h];                      // one block only: y[0] = X_0[P_0[h]]
         }
         // -- as B of pair b - 1: unwind links (Section 4), undelete words --------
+        // Lane L owns the run of positions [p0, p1).  The links of position p
+        // are the predecessor / successor of rank(p) among the ranks of all
+        // positions < p.  The lane's bitset starts as the ranks of all
+        // positions before p0 (each lane sets the bits of its own run, then
+        // an exclusive OR-scan over the lanes), then the lane walks its run,
+        // querying and inserting one rank per position.
         if (b >= 1) {
             const int NB = len;
             const int cs = (NB + 31) >> 5;             // positions per lane (a run)
@@ -285,20 +343,31 @@ sortlist_kernel(SegTable tab)
                 const int r = rk[pos];
                 bw[32 * (r >> 5)] |= 1u << (r & 31);
             }
-            // exclusive OR-scan over lanes: the ranks of all positions before p0
-            uint32_t summ = 0;                          // bit w: word w non-empty
-            for (int w = 0; w < nw; ++w) {
-                uint32_t x = bw[32 * w];
+            __syncwarp();
+            // exclusive OR-scan over lanes, transposed: lane w scans word w of
+            // all 32 runs (read and written in rotated order, bank (i + w) % 32),
+            // so run L's bitset becomes the ranks of all positions before p0
+            if (lane < nw) {
+                uint32_t* col = areaW + 32 * lane;
+                uint32_t c[32];
 #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t y = __shfl_up_sync(kFull, x, off);
-                    if (lane >= off) x |= y;
+                for (int i = 0; i < 32; ++i) c[i] = col[(i + lane) & 31];
+                uint32_t low = 0u;                      // runs 0 .. w-1 (the wrapped tail)
+#pragma unroll
+                for (int i = 0; i < 32; ++i) low |= (i >= 32 - lane) ? c[i] : 0u;
+                uint32_t acc_hi = 0u, acc_lo = 0u;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const bool hi_part = i < 32 - lane;  // run L = i + w >= w
+                    const uint32_t pre = hi_part ? (low | acc_hi) : acc_lo;
+                    acc_hi |= hi_part ? c[i] : 0u;
+                    acc_lo |= hi_part ? 0u : c[i];
+                    col[(i + lane) & 31] = pre;
                 }
-                uint32_t ex = __shfl_up_sync(kFull, x, 1);
-                if (lane == 0) ex = 0u;
-                bw[32 * w] = ex;
-                summ |= ex ? (1u << w) : 0u;
             }
+            __syncwarp();
+            uint32_t summ = 0;                          // bit w: word w non-empty
+            for (int w = 0; w < nw; ++w) summ |= bw[32 * w] ? (1u << w) : 0u;
             // the run: predecessor / successor of rank(pos) among earlier positions
             uint32_t uo[32];
             const uint32_t sentB = (uint32_t)k + 1;

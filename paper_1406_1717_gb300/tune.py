@@ -90,18 +90,18 @@ def autotune(h, device=0, n=1 << 22, seed=20140607, classes=CLASS_K, tier=True) 
         best_g, best_t = 0, float("inf")
         for g in SORT_CANDIDATES:
             mf_set_tuning(h, k, g, 0)
-            t = _time_kernel(h, x, k, "sortmerge")
+            t = _time_kernel(h, x, k, "sort")
             if t < best_t:
                 best_g, best_t = g, t
         best_e, best_te = 0, float("inf")
         for e in STORE_CANDIDATES:
             mf_set_tuning(h, k, best_g, e)
-            t = _time_kernel(h, x, k, "epilogue")
+            t = _time_kernel(h, x, k, "store")
             if t < best_te:
                 best_e, best_te = e, t
         mf_set_tuning(h, k, best_g, best_e)
         result[str(k)] = {"sort_pairs_per_cta": best_g, "store_pairs_per_cta": best_e,
-                          "sortmerge_ms": best_t, "epilogue_ms": best_te}
+                          "sort_ms": best_t, "store_ms": best_te}
     if tier:
         result["tier"] = tune_tier_threshold(h, x)
     return result
