@@ -615,25 +615,51 @@ epilogue_kernel(SegTable tab, int G)
     int32_t* as = p.argmed ? p.argmed + ebase + 1 : nullptr;
     const uint16_t* outs = p.out + (size_t)(j0 - 1) * p.kp;
     const int stride = blockDim.x;
-    // pair by pair (outputs g*k .. g*k + NB - 1 of this CTA); four outputs per
-    // thread per round: loads first, then lookups and stores
-    for (int g = 0, gk = 0; gk < nout; ++g, gk += k) {
-        const int cnt = min(k, nout - gk);
-        const uint16_t* og = outs + (size_t)g * p.kp;
-        for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * stride) {
+    if (k >= 128) {
+        // pair by pair (outputs g*k .. g*k + NB - 1 of this CTA); four outputs
+        // per thread per round: loads first, then lookups and stores
+        for (int g = 0, gk = 0; gk < nout; ++g, gk += k) {
+            const int cnt = min(k, nout - gk);
+            const uint16_t* og = outs + (size_t)g * p.kp;
+            for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * stride) {
+                uint32_t id[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * stride;
+                    id[u] = i < cnt ? (uint32_t)og[i] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * stride;
+                    if (i < cnt) {
+                        const int e = gk + (int)(id[u] >> 15) * k + (int)(id[u] & 0x7fffu);
+                        ys[gk + i] = xs[e];
+                        if (as) as[gk + i] = (int32_t)(ebase + e);
+                    }
+                }
+            }
+        }
+    } else {
+        // small windows: all outputs of the CTA at once (output o = step i of
+        // pair g, o = g k + i; g by an exact multiply-shift, o k < 2^32)
+        const uint64_t kmg = ((1ull << 32) + (uint64_t)k - 1) / (uint64_t)k;
+        for (int o0 = threadIdx.x; o0 < nout; o0 += 4 * stride) {
             uint32_t id[4];
+            int gk[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int i = i0 + u * stride;
-                id[u] = i < cnt ? (uint32_t)og[i] : 0u;
+                const int o = o0 + u * stride;
+                const int g = (int)(((uint64_t)(uint32_t)o * kmg) >> 32);
+                gk[u] = g * k;
+                id[u] = o < nout ? (uint32_t)outs[(size_t)g * p.kp + (o - gk[u])] : 0u;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int i = i0 + u * stride;
-                if (i < cnt) {
-                    const int e = gk + (int)(id[u] >> 15) * k + (int)(id[u] & 0x7fffu);
-                    ys[gk + i] = xs[e];
-                    if (as) as[gk + i] = (int32_t)(ebase + e);
+                const int o = o0 + u * stride;
+                if (o < nout) {
+                    const int e = gk[u] + (int)(id[u] >> 15) * k + (int)(id[u] & 0x7fffu);
+                    ys[o] = xs[e];
+                    if (as) as[o] = (int32_t)(ebase + e);
                 }
             }
         }
@@ -814,6 +840,11 @@ struct ClassPlan {
     int GE;       size_t ebytes;
 };
 
+// Class boundaries: the packed list format ends at k = 1021, the one-word
+// unwind summary at k = 1024; smaller classes keep the shared-memory layouts
+// of small k.
+static const int kClassMax[] = {64, 256, 1021, 2047, 4095, 1 << 30};
+
 // Built-in launch-plan choices per class where a measurement beat the
 // capacity rule (0 = use the rule): on GB300 at k = 1001 (n = 2^26 random
 // walk) 3 pairs per sort CTA took 2.28 ms against 2.39 ms for the largest
@@ -841,8 +872,11 @@ static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tu
     const int cls = tune_class_of(kmax);
     if (tune) tune += cls;
     const int64_t want = (total_pairs + 2ll * num_sms - 1) / (2ll * num_sms);
-    // fused path: 4-byte elements whose lists fit the packed chain format
-    c->fused = !wide && kmax <= kFusedMaxK;
+    // fused path: 4-byte elements whose lists fit the packed chain format,
+    // above the smallest class (GB300, n = 2^24 random walk: the fused sort
+    // took 0.47 ms against 0.89 for sort + unwind at k = 1001 and 0.57 vs
+    // 0.85 at k = 127, but 0.78 vs 0.71 at k = 63 and 9.5 vs 5.5 at k = 3)
+    c->fused = !wide && kmax <= kFusedMaxK && kmax > kClassMax[0];
     c->lwarps = kSortListWarps;
     c->lGcap = 1 << 30;
     if (tune && tune->sort_G > 0) c->lGcap = tune->sort_G;
@@ -870,7 +904,7 @@ static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tu
     // chain
     if (!chain_plan(kmax, &c->cp, &c->cbytes)) return false;
     // epilogue
-    const int GEcap = max(1, min(16, 8192 / kmax));
+    const int GEcap = max(1, 8192 / kmax);              // about 8192 outputs per CTA
     c->GE = kBuiltinEpiG[cls] > 0 ? min(GEcap, kBuiltinEpiG[cls]) : GEcap;
     if (tune && tune->epi_G > 0) c->GE = min(GEcap, tune->epi_G);
     c->ebytes = (wide ? 8ull : 4ull) * (size_t)(c->GE + 1) * kmax;
@@ -984,10 +1018,6 @@ cudaError_t launch_pipeline(const void* x, int64_t n, int k, int rank, Elem el,
     return launch_classes(&cls, &tab, tot, 1, stream, stats);
 }
 
-// Class boundaries: the packed list format ends at k = 1021, the one-word
-// unwind summary at k = 1024; smaller classes keep the shared-memory layouts
-// of small k.
-static const int kClassMax[] = {64, 256, 1021, 2047, 4095, 1 << 30};
 constexpr int kNumClasses = kNumTuneClasses;
 
 int tune_class_of(int k)
