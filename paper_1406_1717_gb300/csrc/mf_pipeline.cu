@@ -327,7 +327,7 @@ struct Lists {
 struct PairState {
     uint32_t mA, wmA, rmA;
     uint32_t mB, wmB, rmB;
-    int sA, sB;
+    int sA;                   // s_B = h - s_A at every step boundary
 };
 
 // One step i of the post-processing (Section 6.2), branch-free: delete(A, i),
@@ -339,7 +339,7 @@ struct PairState {
 template <bool PACKED>
 __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>& L, uint32_t i,
                                               uint32_t wa, uint32_t pb, uint32_t nb, uint32_t rb,
-                                              uint32_t wbw, int h, uint32_t* wnext)
+                                              uint32_t wbw, uint32_t* wnext)
 {
     using LL = Lists<PACKED>;
     // -------- delete(A, i) ----------------------------------------------------
@@ -381,7 +381,10 @@ __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>
     st.wmB = smallB ? wtB : st.wmB;
     if (PACKED) st.rmB = st.wmB >> 20; else st.rmB = smallB ? rtB : st.rmB;
     // -------- advance the list whose first large element is smaller -----------
-    const bool adv = st.sA + st.sB < h;
+    // s_A + s_B = h before the step (eq. inv, Section 6.3); delete(A, i) lowers
+    // s_A exactly when S_A was not empty, and undelete leaves s_B, so the
+    // test "s_A + s_B < h" is "s_A was positive before the delete"
+    const bool adv = sApos;
     const bool aA = st.rmA < st.rmB;                    // peek(A) <= peek(B): A first on ties
     const uint32_t tN = aA ? LL::nxt(st.wmA) : LL::nxt(st.wmB);
     const uint32_t wN = L.ld(tN);
@@ -400,7 +403,6 @@ __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>
         st.rmB = advB ? rN : st.rmB;
     }
     st.sA += advA ? 1 : 0;
-    st.sB += advB ? 1 : 0;
     // -------- print min(peek(A), peek(B)) ------------------------------------
     return st.rmA < st.rmB ? st.mA : (0x8000u | st.mB);
 }
@@ -452,7 +454,6 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
     st.mB = SB;
     st.wmB = L.ld(SB);
     st.rmB = LL::RINF;
-    st.sB = 0;
 
     // ---- the k steps, 8 at a time; inputs of the next two chunks in flight ---
     const uint4* ul4 = reinterpret_cast<const uint4*>(p.ulink + bbase);
@@ -481,7 +482,7 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
                 uint32_t wn;
                 const uint32_t pb = wbv[t] >> 16, nb = wbv[t] & 0xffffu;
                 const uint32_t o = pair_step<PACKED>(st, L, (uint32_t)i, wa, pb, nb, rb,
-                                                     LL::make(pb, nb, rb), h, &wn);
+                                                     LL::make(pb, nb, rb), &wn);
                 wa = wn;
                 ov[t >> 1] |= (t & 1) ? (o << 16) : o;
             }
@@ -530,7 +531,6 @@ __device__ __forceinline__ void chain_body_words(const PipeParams& p, uint32_t* 
     st.mB = (uint32_t)k + 1;
     st.wmB = L.ld(st.mB);
     st.rmB = LL::RINF;
-    st.sB = 0;
 
     // ---- the k steps, 8 at a time; B words of the next two chunks in flight ---
     const uint4* wb4 = reinterpret_cast<const uint4*>(p.wB + (size_t)q * p.kw);
@@ -555,7 +555,7 @@ __device__ __forceinline__ void chain_body_words(const PipeParams& p, uint32_t* 
                 const uint32_t w = wbv[t];
                 uint32_t wn;
                 const uint32_t o = pair_step<true>(st, L, (uint32_t)i, wa, LL::prv(w), LL::nxt(w),
-                                                   w >> 20, w, h, &wn);
+                                                   w >> 20, w, &wn);
                 wa = wn;
                 ov[t >> 1] |= (t & 1) ? (o << 16) : o;
             }
@@ -615,7 +615,7 @@ epilogue_kernel(SegTable tab, int G)
     int32_t* as = p.argmed ? p.argmed + ebase + 1 : nullptr;
     const uint16_t* outs = p.out + (size_t)(j0 - 1) * p.kp;
     const int stride = blockDim.x;
-    if (k >= 128) {
+    if (k >= 512) {
         // pair by pair (outputs g*k .. g*k + NB - 1 of this CTA); four outputs
         // per thread per round: loads first, then lookups and stores
         for (int g = 0, gk = 0; gk < nout; ++g, gk += k) {

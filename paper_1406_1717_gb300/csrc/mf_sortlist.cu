@@ -385,7 +385,9 @@ sortlist_kernel(SegTable tab)
                     const uint32_t shi = summ & ~((2u << w) - 1u);
                     const int wlo = slo ? 31 - __clz(slo) : 0;
                     const int whi = shi ? __ffs(shi) - 1 : 0;
-                    const uint32_t xlo = bw[32 * wlo], xhi = bw[32 * whi];
+                    uint32_t xlo = 0u, xhi = 0u;            // the nearest non-empty words, when needed
+                    if (!mlo && slo) xlo = bw[32 * wlo];
+                    if (!mhi && shi) xhi = bw[32 * whi];
                     const int pred = mlo ? ((w << 5) | (31 - __clz(mlo)))
                                          : (slo ? ((wlo << 5) | (31 - __clz(xlo))) : -1);
                     const int succ = mhi ? ((w << 5) | (__ffs(mhi) - 1))
