@@ -62,7 +62,8 @@ def test_small_uniform_k31_full(handle):
     check_full(handle, uniform_f32(100_000), 31, "uniform k=31")
 
 
-@pytest.mark.parametrize("k", [1, 3, 5, 31, 33, 63, 65, 127, 255, 1001, 1023, 1025, 2047, 4095])
+@pytest.mark.parametrize("k", [1, 3, 5, 31, 33, 63, 65, 127, 129, 255, 341, 511, 513, 1001, 1021, 1023,
+                               1025, 2047, 4095])
 def test_block_boundary_sizes(handle, k):
     rng = np.random.default_rng(k)
     for n in sorted({k, k + 1, 2 * k - 1, 2 * k, 2 * k + 1, 5 * k, 5 * k + int(rng.integers(1, k + 1)),
