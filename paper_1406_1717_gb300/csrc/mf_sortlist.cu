@@ -46,10 +46,17 @@ namespace {
 
 constexpr int kTileU64 = kTileElems + kTileElems / 32;    // padded tile in 8-byte words
 constexpr uint32_t kTileBytes = kTileU64 * 8;
+static_assert(2 * kTileElems + 2 * (kTileElems + kTileElems / 16) + 4 * (kTileElems + kTileElems / 32) <=
+              (int)kTileBytes, "perm, padded rank and bitset/link area fit in a tile");
 constexpr uint64_t kPadComp = ~0ull;                       // above every composite
 constexpr uint32_t kRankInf = 0x7ffu;                      // sentinel rank (11 bits)
 
 __device__ __forceinline__ int tix(int x) { return x + (x >> 5); }
+// Padded index of the 16-bit rank array: two entries of padding per 32, so
+// the 32 lanes of a warp reading entries 32 L + i (one run each) hit 32
+// different banks (17 L + i / 2 mod 32) instead of two.
+__device__ __forceinline__ int rix(int x) { return x + ((x >> 5) << 1); }
+constexpr int kRankU16 = kTileElems + kTileElems / 16;   // 1088 entries
 
 template <typename V>
 __host__ __device__ __forceinline__ void cmpx(V& a, V& b)
@@ -270,10 +277,11 @@ sortlist_kernel(SegTable tab)
 
     // ---- 4. per block of the tile ------------------------------------------------
     // The tile becomes: perm (u16, by sorted index), rank (u16, by block
-    // position) and a 4352-byte area for bitsets, then unwind links.
+    // position, padded: rix) and a 4224-byte area for bitsets, then unwind
+    // links (2048 + 2176 + 4224 = 8448 bytes).
     uint16_t* permW = reinterpret_cast<uint16_t*>(T);
     uint16_t* rnkW = permW + kTileElems;
-    uint32_t* areaW = reinterpret_cast<uint32_t*>(rnkW + kTileElems);
+    uint32_t* areaW = reinterpret_cast<uint32_t*>(rnkW + kRankU16);
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = T[tix(lane + 32 * i)];
     __syncwarp();
@@ -284,7 +292,7 @@ sortlist_kernel(SegTable tab)
             const uint32_t pos = comp_pos(v[i]);
             const uint32_t blk = (uint32_t)(v[i] >> 42);
             permW[x] = (uint16_t)pos;
-            rnkW[blk * k + pos] = (uint16_t)(x - blk * k);
+            rnkW[rix(blk * k + pos)] = (uint16_t)(x - blk * k);
         }
     }
     __syncwarp();
@@ -295,7 +303,6 @@ sortlist_kernel(SegTable tab)
         const int boff = bt * k;
         const int len = min(k, tile_n - boff);
         const uint16_t* pm = permW + boff;
-        const uint16_t* rk = rnkW + boff;
         // -- as A of pair b: construct(A) in slot space (Section 5.3) -------------
         if (b < npair) {
             uint32_t* wa = p.wA + (size_t)(j0 - 1 + b) * p.kw;
@@ -306,7 +313,7 @@ sortlist_kernel(SegTable tab)
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int pos = pos0 + 32 * u;
-                    t[u] = pos < k ? (int)rk[pos] : 0;
+                    t[u] = pos < k ? (int)rnkW[rix(boff + pos)] : 0;
                     jv[u] = pos < k ? (uint32_t)ja[pos] : 0u;
                 }
 #pragma unroll
@@ -340,7 +347,7 @@ sortlist_kernel(SegTable tab)
             uint32_t* bw = areaW + lane;                // word w of this lane at bw[32 w]
             for (int w = 0; w < nw; ++w) bw[32 * w] = 0u;
             for (int pos = p0; pos < p1; ++pos) {
-                const int r = rk[pos];
+                const int r = rnkW[rix(boff + pos)];
                 bw[32 * (r >> 5)] |= 1u << (r & 31);
             }
             __syncwarp();
@@ -376,7 +383,7 @@ sortlist_kernel(SegTable tab)
                 uo[i] = 0u;
                 const int pos = p0 + i;
                 if (pos < p1) {
-                    const int r = rk[pos];
+                    const int r = rnkW[rix(boff + pos)];
                     const int w = r >> 5, bb = r & 31;
                     const uint32_t word = bw[32 * w];
                     const uint32_t mlo = word & ((1u << bb) - 1u);
