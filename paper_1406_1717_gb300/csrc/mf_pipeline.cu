@@ -608,7 +608,35 @@ epilogue_kernel(SegTable tab, int G)
     const int64_t rem = p.n - ebase;
     const int E = (int)((int64_t)(npair + 1) * k < rem ? (int64_t)(npair + 1) * k : rem);
     const ValT* xp = reinterpret_cast<const ValT*>(p.x);
-    for (int e = threadIdx.x; e < E; e += blockDim.x) xs[e] = __ldg(xp + ebase + e);
+    if (sizeof(ValT) == 4) {
+        // the span's 16-byte-aligned interior as uint4, the ragged ends one by one
+        const uint32_t* xs4 = reinterpret_cast<const uint32_t*>(xp + ebase);
+        uint32_t* xd = reinterpret_cast<uint32_t*>(xs);
+        const int head = min(E, (int)(((16u - ((uint32_t)(uintptr_t)xs4 & 15u)) & 15u) >> 2));
+        const int nvec = (E - head) >> 2;
+        const int tail0 = head + 4 * nvec;
+        const uint4* xv = reinterpret_cast<const uint4*>(xs4 + head);
+        for (int c0 = threadIdx.x; c0 < nvec; c0 += 4 * blockDim.x) {
+            uint4 r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + u * (int)blockDim.x;
+                r[u] = c < nvec ? __ldg(xv + c) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + u * (int)blockDim.x;
+                if (c < nvec) {
+                    uint32_t* d = xd + head + 4 * c;
+                    d[0] = r[u].x; d[1] = r[u].y; d[2] = r[u].z; d[3] = r[u].w;
+                }
+            }
+        }
+        if ((int)threadIdx.x < head) xd[threadIdx.x] = __ldg(xs4 + threadIdx.x);
+        if ((int)threadIdx.x < E - tail0) xd[tail0 + threadIdx.x] = __ldg(xs4 + tail0 + threadIdx.x);
+    } else {
+        for (int e = threadIdx.x; e < E; e += blockDim.x) xs[e] = __ldg(xp + ebase + e);
+    }
     __syncthreads();
     const int nout = npair > 0 ? E - k : 0;
     ValT* ys = reinterpret_cast<ValT*>(p.y) + ebase + 1;
