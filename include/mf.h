@@ -128,11 +128,13 @@ mf_status mf_filter_rank(mf_handle h, mf_dtype dtype, const void* x, int64_t n, 
 
 /* Same as mf_filter, but x, y and argmed are HOST pointers.  The call copies
  * x to the handle's device workspace, filters, copies y (and argmed) back and
- * waits for the stream: it is synchronous.  Signals of more than 2^20 outputs
- * run in up to four chunks of outputs (each with its k-1 input halo) on the
- * handle's stream and a second stream of the handle, so that one chunk's
- * copies overlap another chunk's kernels; the results equal one whole call.
- * Pinned host memory gives the fastest copies; pageable memory works.
+ * waits: it is synchronous.  Signals of more than 2^20 outputs run in up to
+ * eight chunks of outputs (each with its k-1 input halo) as a pipeline on
+ * three streams: copies in on a stream of the handle, the filter on the
+ * handle's stream, copies out on a third, chained by events, with three
+ * chunk buffers in flight; so one chunk's copies overlap the filtering of
+ * the others, and copies in overlap copies out.  The results equal one whole
+ * call.  Pinned host memory gives the fastest copies; pageable memory works.
  * Errors: as mf_filter, plus MF_ERR_OOM (workspace). */
 mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_t n, int32_t k,
                          void* y_host, int32_t* argmed_host);

@@ -32,9 +32,13 @@ struct mf_ctx {
     bool stage_in_graph;
     cudaEvent_t stage_done;
     std::vector<void*> retired;
-    // second stream and fork / join events of the chunked host entry point
-    cudaStream_t aux = nullptr;
+    // copy-in and copy-out streams of the chunked host entry point, the
+    // fork / join events and, per buffer slot, the events that chain a
+    // chunk's copy-in, filter and copy-out
+    cudaStream_t aux = nullptr, aux2 = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    static constexpr int kHostSlots = 3;
+    cudaEvent_t ev_in[kHostSlots] = {}, ev_done[kHostSlots] = {}, ev_out[kHostSlots] = {};
 };
 
 namespace {
@@ -232,13 +236,14 @@ mf_status mf_filter_rank(mf_handle h, mf_dtype dtype, const void* x, int64_t n, 
     return filter_device(h, dtype, x, n, k, rank, y, argmed);
 }
 
-// Outputs per chunk of the host entry point: the copies of one chunk overlap
-// the kernels of the other stream's chunk, so chunks of about 1/4 of the
-// signal (measured at n = 2^26, pinned buffers: 6.40 ms per call with 4
-// chunks, 6.59 with 8, 7.04 with 16, 7.65 unchunked), at least 2^20
-// outputs, and a multiple of k.
+// Outputs per chunk of the host entry point: about 1/8 of the signal, at
+// least 2^20 outputs, a multiple of k.  The chunks run as a pipeline on three
+// streams -- copy-in, filter (the handle's stream), copy-out -- chained by one
+// event per step, with kHostSlots device buffer slots in flight; so the
+// copies of one chunk overlap the filtering of its neighbours, and H2D and
+// D2H (separate copy engines) overlap each other.
 static int64_t host_chunk_outputs(int64_t m, int k) {
-    const int64_t target = std::max<int64_t>((m + 3) / 4, (int64_t)1 << 20);
+    const int64_t target = std::max<int64_t>((m + 7) / 8, (int64_t)1 << 20);
     return (target + k - 1) / k * k;
 }
 
@@ -258,61 +263,78 @@ mf_status mf_filter_host(mf_handle h, mf_dtype dtype, const void* x_host, int64_
     // every window lies inside one chunk, so the results equal one whole call.
     const int64_t L = host_chunk_outputs(m, k);
     const int64_t nchunks = (m + L - 1) / L;
-    const int nslots = nchunks > 1 ? 2 : 1;
+    constexpr int R = mf_ctx::kHostSlots;
+    const int nslots = (int)std::min<int64_t>(nchunks, R);
     const int64_t cin = std::min<int64_t>(n, L + k - 1);
     const size_t xb = (eb * (size_t)cin + 255) & ~size_t(255);
     const size_t yb = (eb * (size_t)L + 255) & ~size_t(255);
     const size_t ab = argmed_host ? ((4 * (size_t)L + 255) & ~size_t(255)) : 0;
     const size_t need = signal_workspace_bytes(h, cin, k, el.wide);
-    const size_t slot_bytes = xb + yb + ab + ((need + 255) & ~size_t(255));
-    st = ensure_workspace(h, slot_bytes * nslots);
+    const size_t slot_bytes = xb + yb + ab;
+    const size_t ws_off = slot_bytes * (size_t)nslots;   // one filter workspace, after the slots
+    st = ensure_workspace(h, ws_off + ((need + 255) & ~size_t(255)));
     if (st != MF_OK) return st;
-    if (nslots > 1 && !h->aux) {
-        if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    if (!h->aux) {
+        bool ok = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) == cudaSuccess;
+        for (int r = 0; ok && r < R; ++r)
+            ok = cudaEventCreateWithFlags(&h->ev_in[r], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->ev_done[r], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->ev_out[r], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
             cudaGetLastError();
             return MF_ERR_CUDA;
         }
     }
-    cudaStream_t streams[2] = {h->stream, h->aux};
-    cudaError_t e = cudaSuccess;
-    if (nslots > 1) {                                   // aux starts after earlier work
-        e = cudaEventRecord(h->fork_ev, h->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->fork_ev, 0);
-    }
+    cudaStream_t sin = h->aux, sfl = h->stream, sout = h->aux2;
+    // both copy streams start after the work already on the handle's stream
+    cudaError_t e = cudaEventRecord(h->fork_ev, sfl);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, h->fork_ev, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, h->fork_ev, 0);
+    void* wsd = (char*)h->ws + ws_off;
     for (int64_t c = 0; c < nchunks && e == cudaSuccess; ++c) {
-        const int slot = (int)(c % nslots);
-        cudaStream_t s = streams[slot];
+        const int slot = (int)(c % R);
         char* base = (char*)h->ws + slot_bytes * slot;
         void* xd = base;
         void* yd = base + xb;
         int32_t* ad = argmed_host ? (int32_t*)(base + xb + yb) : nullptr;
-        void* wsd = base + xb + yb + ab;
         const int64_t off = c * L;
         const int64_t out = std::min(L, m - off);
         const int64_t in = out + k - 1;
-        e = cudaMemcpyAsync(xd, (const char*)x_host + eb * off, eb * (size_t)in,
-                            cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = launch_signal(h, xd, in, k, rank, el, yd, ad, wsd, need, s);
+        // copy-in, once the slot's previous chunk has been copied out
+        if (c >= R) e = cudaStreamWaitEvent(sin, h->ev_out[slot], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(xd, (const char*)x_host + eb * off, eb * (size_t)in,
+                                cudaMemcpyHostToDevice, sin);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[slot], sin);
+        // filter
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sfl, h->ev_in[slot], 0);
+        if (e == cudaSuccess) e = launch_signal(h, xd, in, k, rank, el, yd, ad, wsd, need, sfl);
         if (e == cudaSuccess && ad && off > 0) {
-            add_offset_kernel<<<(unsigned)((out + 255) / 256), 256, 0, s>>>(ad, out, (int32_t)off);
+            add_offset_kernel<<<(unsigned)((out + 255) / 256), 256, 0, sfl>>>(ad, out, (int32_t)off);
             h->stats.launches += 1;
             e = cudaGetLastError();
         }
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_done[slot], sfl);
+        // copy-out
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, h->ev_done[slot], 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync((char*)y_host + eb * off, yd, eb * (size_t)out,
-                                cudaMemcpyDeviceToHost, s);
+                                cudaMemcpyDeviceToHost, sout);
         if (e == cudaSuccess && ad)
-            e = cudaMemcpyAsync(argmed_host + off, ad, 4 * (size_t)out, cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(argmed_host + off, ad, 4 * (size_t)out, cudaMemcpyDeviceToHost, sout);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_out[slot], sout);
     }
-    if (nslots > 1) {                                   // the handle's stream waits for aux
-        const cudaError_t e2 = cudaEventRecord(h->join_ev, h->aux);
-        if (e2 == cudaSuccess) cudaStreamWaitEvent(h->stream, h->join_ev, 0);
-        if (e == cudaSuccess) e = e2;
-    }
-    const cudaError_t e3 = cudaStreamSynchronize(h->stream);
+    // the handle's stream waits for the last copy-out (and the copy-in stream)
+    const cudaError_t e2 = cudaEventRecord(h->join_ev, sout);
+    if (e2 == cudaSuccess) cudaStreamWaitEvent(sfl, h->join_ev, 0);
+    if (e == cudaSuccess) e = e2;
+    const cudaError_t e3 = cudaStreamSynchronize(sfl);
+    const cudaError_t e4 = cudaStreamSynchronize(sin);
     if (e == cudaSuccess) e = e3;
+    if (e == cudaSuccess) e = e4;
     return cuda_status(e);
 }
 
@@ -567,9 +589,16 @@ mf_status mf_destroy(mf_handle h) {
             cudaEventDestroy(h->stage_done);
             if (h->aux) {
                 cudaStreamSynchronize(h->aux);
+                cudaStreamSynchronize(h->aux2);
                 cudaStreamDestroy(h->aux);
+                cudaStreamDestroy(h->aux2);
                 cudaEventDestroy(h->fork_ev);
                 cudaEventDestroy(h->join_ev);
+                for (int r = 0; r < mf_ctx::kHostSlots; ++r) {
+                    cudaEventDestroy(h->ev_in[r]);
+                    cudaEventDestroy(h->ev_done[r]);
+                    cudaEventDestroy(h->ev_out[r]);
+                }
             }
             if (h->stage) cudaFreeHost(h->stage);
             for (void* r : h->retired) cudaFreeHost(r);
