@@ -900,11 +900,8 @@ static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tu
     const int cls = tune_class_of(kmax);
     if (tune) tune += cls;
     const int64_t want = (total_pairs + 2ll * num_sms - 1) / (2ll * num_sms);
-    // fused path: 4-byte elements whose lists fit the packed chain format,
-    // above the smallest class (GB300, n = 2^24 random walk: the fused sort
-    // took 0.47 ms against 0.89 for sort + unwind at k = 1001 and 0.57 vs
-    // 0.85 at k = 127, but 0.78 vs 0.71 at k = 63 and 9.5 vs 5.5 at k = 3)
-    c->fused = !wide && kmax <= kFusedMaxK && kmax > kClassMax[0];
+    // fused path: 4-byte elements whose lists fit the packed chain format
+    c->fused = !wide && kmax <= kFusedMaxK;
     c->lwarps = kSortListWarps;
     c->lGcap = 1 << 30;
     if (tune && tune->sort_G > 0) c->lGcap = tune->sort_G;

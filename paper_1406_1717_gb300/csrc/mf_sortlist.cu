@@ -298,6 +298,49 @@ sortlist_kernel(SegTable tab)
     __syncwarp();
 
     const int nbt = (tile_n + k - 1) / k;
+    if (k <= 64) {
+        // Small windows (16 or more blocks per tile): one lane per block.  All
+        // ranks of a block are below 64, so the ranks of the positions before
+        // p form one 64-bit register; its bits below / above rank(p) give the
+        // unwind links of p directly.
+        for (int bt = lane; bt < nbt; bt += 32) {
+            const int b = warp * bpw + bt;              // block of the CTA
+            const int boff = bt * k;
+            const int len = min(k, tile_n - boff);
+            const uint16_t* pm = permW + boff;
+            if (b < npair) {                            // as A: construct(A) words
+                uint32_t* wa = p.wA + (size_t)(j0 - 1 + b) * p.kw;
+                const uint16_t* ja = jaS + (size_t)b * k;
+                for (int pos = 0; pos < k; ++pos) {
+                    const int t = rnkW[rix(boff + pos)];
+                    const uint32_t pv = t > 0 ? pm[t - 1] : (uint32_t)k;
+                    const uint32_t nx = t + 1 < k ? pm[t + 1] : (uint32_t)k;
+                    wa[pos] = nx | (pv << 10) | ((uint32_t)ja[pos] << 20);
+                }
+                wa[k] = (uint32_t)pm[0] | ((uint32_t)pm[k - 1] << 10) | (kRankInf << 20);
+                wa[k + 1] = (uint32_t)(k + 1) | ((uint32_t)(k + 1) << 10) | (kRankInf << 20);
+                wa[k + 2] = pm[p.h];
+            } else if (npair == 0) {
+                p.wA[k + 2] = pm[p.h];                  // one block only: y[0] = X_0[P_0[h]]
+            }
+            if (b >= 1) {                               // as B of pair b - 1: unwind(B) links
+                uint32_t* wb = p.wB + (size_t)(j0 - 1 + b - 1) * p.kw;
+                const uint16_t* jb = jbS + (size_t)(b - 1) * k;
+                const uint32_t sentB = (uint32_t)k + 1;
+                uint64_t seen = 0ull;                   // ranks of positions before pos
+                for (int pos = 0; pos < len; ++pos) {
+                    const int r = rnkW[rix(boff + pos)];
+                    const uint64_t below = seen & ((1ull << r) - 1ull);
+                    const uint64_t above = seen & ~((2ull << r) - 1ull);   // r = 63: 0
+                    const uint32_t pv = below ? (uint32_t)pm[63 - __clzll((long long)below)] : sentB;
+                    const uint32_t nx = above ? (uint32_t)pm[__ffsll((long long)above) - 1] : sentB;
+                    wb[pos] = nx | (pv << 10) | ((uint32_t)jb[pos] << 20);
+                    seen |= 1ull << r;
+                }
+            }
+        }
+        return;
+    }
     for (int bt = 0; bt < nbt; ++bt) {
         const int b = warp * bpw + bt;                  // block of the CTA
         const int boff = bt * k;
