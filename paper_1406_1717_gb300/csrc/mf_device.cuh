@@ -2,7 +2,9 @@
 //
 // Paper: "Median Filtering is Equivalent to Sorting" (Suomela).
 //  * order keys ............ Section 5.2 (the stable sort compares (alpha[i], i))
-//  * warp radix sort ....... Section 3 "Piecewise Sorting" / Section 6.1
+//  * warp radix sort ....... Section 3 "Piecewise Sorting" / Section 6.1 (the
+//                            four-kernel path: 8-byte elements, k > 1021)
+//  * signal / work-item lookup of batched launches
 //  * pair merge ............ joint ranks of the two blocks of a pair: the
 //                            rank-space form of the comparisons of Section 5.3
 //                            ("(alpha[i], i) < (alpha[m], m)") and of the

@@ -63,10 +63,7 @@ struct UnwindPlan {
 // its list words.  Packed chain format only (slots fit in 10 bits).
 constexpr int kFusedMaxK = 1021;
 constexpr int kTileElems = 1024;                 // elements per warp tile
-constexpr int kSortListWarps = 8;
-struct ListPlan {
-    int warps;                // warps per CTA (tiles)
-};
+constexpr int kSortListWarps = 8;          // warps (tiles) per sortlist CTA
 struct ChainPlan {
     bool packed;              // one 32-bit word per list node (k <= 1021)
     int nwarps;
