@@ -916,7 +916,11 @@ static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tu
     UnwindPlan& up = c->up;
     up.nw = (kmax + 31) / 32;
     up.ns = up.nw <= 32 ? 0 : (up.nw + 31) / 32;
-    up.segs = kmax >= 256 ? 4 : (kmax >= 64 ? 2 : 1);
+    // runs per block: more runs shorten each lane's serial walk at the cost of
+    // seeding each run with the ranks of all earlier positions (GB300,
+    // n = 2^24: unwind at k = 4095 took 1.42 ms with 4 runs, 0.72 ms with 32;
+    // float64 at k = 1001 0.285 ms with 4, 0.195 with 8, 0.264 with 32)
+    up.segs = kmax > 1024 ? 32 : (kmax >= 256 ? 8 : (kmax >= 64 ? 2 : 1));
     up.seglen = (((kmax + up.segs - 1) / up.segs) + 7) & ~7;
     c->bpw = 32 / up.segs;
     const int kpmax = (kmax + 7) & ~7;
