@@ -39,6 +39,45 @@ namespace mf {
 // ===========================================================================
 // sortmerge_kernel
 // ===========================================================================
+// One merge round over the parts of every block of the CTA: within a block
+// (start b k, length min(k, E - b k)) the runs [g, g + w) and [g + w, g + 2w),
+// g a multiple of 2w, are merged, the left run first on equal keys.  Thread t
+// writes a contiguous span of the CTA's outputs, split where a merge ends;
+// each piece finds its start by a merge-path search.
+template <typename KeyT>
+__device__ void merge_runs(const KeyT* ks, const uint16_t* vs, KeyT* kd, uint16_t* vd,
+                           int E, int k, int w)
+{
+    const int C = (E + (int)blockDim.x - 1) / (int)blockDim.x;
+    int e = (int)threadIdx.x * C;
+    const int eend = min(e + C, E);
+    while (e < eend) {
+        const int bstart = (e / k) * k;
+        const int blen = min(k, E - bstart);
+        const int off = e - bstart;
+        const int g0 = off - off % (2 * w);
+        const int L1 = min(g0 + w, blen), R1 = min(g0 + 2 * w, blen);
+        const int na = L1 - g0, nb = R1 - L1;
+        const int pend = min(eend, bstart + R1);
+        const int d = off - g0;
+        const KeyT* A = ks + bstart + g0;
+        const KeyT* B = ks + bstart + L1;
+        const uint16_t* VA = vs + bstart + g0;
+        const uint16_t* VB = vs + bstart + L1;
+        int lo = max(0, d - nb), hi = min(d, na);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A[mid] <= B[d - 1 - mid]) lo = mid + 1; else hi = mid;
+        }
+        int ia = lo, ib = d - lo;
+        for (int o = e; o < pend; ++o) {
+            if (ib >= nb || (ia < na && A[ia] <= B[ib])) { kd[o] = A[ia]; vd[o] = VA[ia]; ++ia; }
+            else { kd[o] = B[ib]; vd[o] = VB[ib]; ++ib; }
+        }
+        e = pend;
+    }
+}
+
 // KeyT: uint32_t for 4-byte elements, uint64_t for 8-byte elements.
 template <typename KeyT>
 __global__ void __launch_bounds__(kPipeThreads)
@@ -75,16 +114,50 @@ sortmerge_kernel(SegTable tab, SortPlan sp)
     }
     __syncthreads();
 
-    const int ngroups = (nblk + bpg - 1) / bpg;
-    for (int gi = warp; gi < ngroups; gi += W) {
-        const int b0 = gi * bpg;
-        const int b1 = min(b0 + bpg, nblk);
-        const int e0 = b0 * k;
-        const int e1 = min(b1 * k, E);
-        warp_sort_group<KeyT>(keyA + e0, valA + e0, keyB + e0, valB + e0,
-                        max(0, e1 - e0), e0, k, b1 - b0, hist + warp * 256);
+    // Long blocks, fewer than half as many as warps: each block is split into
+    // H position-contiguous parts (H = 2 or 4), a warp sorts each part and
+    // merge rounds of all threads join them.  Still a stable sort: the parts
+    // are in position order and a merge takes the left run first on ties.
+    int H = 1;
+    if (k >= 512)
+        while (H < 4 && nblk * H * 2 <= W) H <<= 1;
+    if (H == 1) {
+        const int ngroups = (nblk + bpg - 1) / bpg;
+        for (int gi = warp; gi < ngroups; gi += W) {
+            const int b0 = gi * bpg;
+            const int b1 = min(b0 + bpg, nblk);
+            const int e0 = b0 * k;
+            const int e1 = min(b1 * k, E);
+            warp_sort_group<KeyT>(keyA + e0, valA + e0, keyB + e0, valB + e0,
+                            max(0, e1 - e0), e0, k, b1 - b0, hist + warp * 256);
+        }
+        __syncthreads();
+    } else {
+        const int part = (k + H - 1) / H;
+        for (int gi = warp; gi < nblk * H; gi += W) {
+            const int b = gi / H, hp = gi - b * H;
+            const int bstart = b * k;
+            const int blen = min(k, E - bstart);
+            const int s0 = min(hp * part, blen), s1 = min(s0 + part, blen);
+            if (s1 > s0)
+                warp_sort_group<KeyT>(keyA + bstart + s0, valA + bstart + s0, keyB + bstart + s0,
+                                      valB + bstart + s0, s1 - s0, bstart + s0, k, 1,
+                                      hist + warp * 256);
+        }
+        __syncthreads();
+        KeyT* ks = keyA;  uint16_t* vs = valA;
+        KeyT* kd = keyB;  uint16_t* vd = valB;
+        for (int w = part; w < k; w <<= 1) {
+            merge_runs<KeyT>(ks, vs, kd, vd, E, k, w);
+            __syncthreads();
+            KeyT* tk = ks; ks = kd; kd = tk;
+            uint16_t* tv = vs; vs = vd; vd = tv;
+        }
+        if (ks != keyA) {
+            for (int e = tid; e < E; e += blockDim.x) { keyA[e] = ks[e]; valA[e] = vs[e]; }
+            __syncthreads();
+        }
     }
-    __syncthreads();
 
     // inverse permutation (rank of each position) into valB, block by block
     for (int blk = 0, bstart = 0; bstart < E; ++blk, bstart += k) {
