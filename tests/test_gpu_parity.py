@@ -112,6 +112,20 @@ def test_int32_extremes_and_ties(handle):
     check_full(handle, np.full(10_000, 5, np.int32), 101, "constant")
 
 
+@pytest.mark.parametrize("k", [1023, 2047, 3001, 4095])
+def test_long_block_sort_heavy_ties(handle, k):
+    """Five distinct values over blocks long enough that the sort splits each
+    block into runs and joins them by merging: equal keys must stay in index
+    order across the run boundaries (the stable sort of Section 6.1)."""
+    rng = np.random.default_rng(k + 11)
+    for n in (5 * k + int(rng.integers(1, k)), 9 * k):
+        x = rng.integers(-2, 3, size=n).astype(np.int32)
+        check_full(handle, x, k, f"5 values n={n} k={k}")
+        f = np.where(rng.random(n) < 0.5, np.float32(-0.0), np.float32(0.0))
+        f[rng.random(n) < 0.1] = np.float32(1.5)
+        check_full(handle, f.astype(np.float32), k, f"signed zeros n={n} k={k}")
+
+
 def test_impulse_noise_ties(handle):
     b = batched_signals(nseg=8, seed=5)
     for s in range(8):
