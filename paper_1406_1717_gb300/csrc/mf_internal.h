@@ -32,6 +32,7 @@ struct PipeParams {
     int lG;                   // block pairs per sortlist CTA
     int bpw;                  // blocks per warp tile (kTileElems / k)
     uint64_t kmagic, bmagic;  // ceil(2^32 / k), ceil(2^32 / bpw): exact division of tile indices
+    int eG;                   // block pairs per epilogue CTA
     int64_t start[4];         // batched launches: this signal's first item per kernel
 };
 

@@ -667,13 +667,13 @@ chain_kernel(SegTable tab, ChainPlan cp)
 // ===========================================================================
 template <typename ValT>
 __global__ void __launch_bounds__(kPipeThreads)
-epilogue_kernel(SegTable tab, int G)
+epilogue_kernel(SegTable tab)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     ValT* xs = reinterpret_cast<ValT*>(smem);
     int64_t cta;
     const PipeParams p = find_signal(tab, kItemEpilogue, blockIdx.x, &cta);
-    const int k = p.k;
+    const int k = p.k, G = p.eG;
     const int64_t j0 = 1 + cta * G;
     const int64_t left = p.npairs - (j0 - 1);
     const int npair = (int)(left < G ? (left > 0 ? left : 0) : G);
@@ -896,6 +896,7 @@ static void fill_signal(PipeParams& p, const void* x, void* y, int32_t* argmed,
     p.npairs = p.nblocks - 1;
     p.kp = (k + 7) & ~7;
     p.is_float = is_float;
+    p.eG = 1;
 }
 
 size_t pipeline_workspace_bytes(int64_t n, int k)
@@ -1016,10 +1017,13 @@ static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tu
 static void count_items(PipeParams& p, const ClassPlan& c, int64_t* tot)
 {
     const int64_t np = p.npairs;
+    // store CTAs cover the class's span of (GE + 1) kmax elements whatever the
+    // signal's own k, so a batch's small windows do not get tiny CTAs
+    p.eG = p.k >= c.kmax ? c.GE : max(1, (int)(((int64_t)(c.GE + 1) * c.kmax) / p.k) - 1);
     int64_t cnt[4] = {np > 0 ? (np + c.sp.G - 1) / c.sp.G : 1,
                       np > 0 ? (np + c.bpw - 1) / c.bpw : 0,
                       np,
-                      np > 0 ? (np + c.GE - 1) / c.GE : 1};
+                      np > 0 ? (np + p.eG - 1) / p.eG : 1};
     if (c.fused) {
         p.bpw = kTileElems / p.k;
         p.lG = max(1, min(c.lwarps * p.bpw - 1, c.lGcap));
@@ -1089,9 +1093,9 @@ static cudaError_t launch_classes(const ClassPlan* cls, const SegTable* tabs, co
     TIMER_MARK(3);
     for (int c = 0; c < ncls; ++c) {
         if (cls[c].wide)
-            epilogue_kernel<uint64_t><<<(unsigned)tot[c][kItemEpilogue], kPipeThreads, cls[c].ebytes, stream>>>(tabs[c], cls[c].GE);
+            epilogue_kernel<uint64_t><<<(unsigned)tot[c][kItemEpilogue], kPipeThreads, cls[c].ebytes, stream>>>(tabs[c]);
         else
-            epilogue_kernel<uint32_t><<<(unsigned)tot[c][kItemEpilogue], kPipeThreads, cls[c].ebytes, stream>>>(tabs[c], cls[c].GE);
+            epilogue_kernel<uint32_t><<<(unsigned)tot[c][kItemEpilogue], kPipeThreads, cls[c].ebytes, stream>>>(tabs[c]);
         if (stats) stats->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -32,6 +32,8 @@
 //      sentinel words and m_A = pi[h]); as B, the unwind links from prefix
 //      bitsets of ranks (32 lanes, each a run of consecutive positions seeded
 //      with the ranks of all positions before it) and the undelete words.
+//      Tiles of many short blocks share the warp out differently: one lane per
+//      block for k <= 64, groups of 4 or 8 lanes per block for k <= 256.
 // Shared memory per warp: the padded tile (8448 bytes; element x at x + x/32
 // so the lane-major stores of step 1 and the merge write-backs are free of
 // bank conflicts), plus 4 KB per warp of joint-rank rows.
@@ -338,6 +340,117 @@ sortlist_kernel(SegTable tab)
                     seen |= 1ull << r;
                 }
             }
+        }
+        return;
+    }
+    if (k <= 256) {
+        // 64 < k <= 256 (four to fifteen blocks per tile): the construct(A)
+        // words of all the tile's blocks at once, then the unwind in groups
+        // of R lanes per block (R = 4 or 8, runs of at most 32 positions),
+        // 32 / R blocks at a time, each group's prefix bitsets by an exclusive
+        // OR-scan of shuffles within the group.  (GB300, n = 2^24 random walk:
+        // the sort kernel at k = 127 took 0.58 ms one block at a time and
+        // 0.43 ms grouped; at k = 511, with R = 16, grouping was 3 % slower.)
+        for (int x = lane; x < tile_n; x += 32) {
+            const int bt = (int)udiv((uint32_t)x, p.kmagic);
+            const int b = warp * bpw + bt;
+            if (b >= npair) continue;                   // full blocks: only the last is ragged
+            const int pos = x - bt * k;
+            const uint16_t* pm = permW + bt * k;
+            const int t = rnkW[rix(x)];
+            const uint32_t pv = t > 0 ? pm[t - 1] : (uint32_t)k;
+            const uint32_t nx = t + 1 < k ? pm[t + 1] : (uint32_t)k;
+            p.wA[(size_t)(j0 - 1 + b) * p.kw + pos] =
+                nx | (pv << 10) | ((uint32_t)jaS[(size_t)b * k + pos] << 20);
+        }
+        for (int bt = lane; bt < nbt; bt += 32) {
+            const int b = warp * bpw + bt;
+            const uint16_t* pm = permW + bt * k;
+            if (b < npair) {
+                uint32_t* wa = p.wA + (size_t)(j0 - 1 + b) * p.kw;
+                wa[k] = (uint32_t)pm[0] | ((uint32_t)pm[k - 1] << 10) | (kRankInf << 20);
+                wa[k + 1] = (uint32_t)(k + 1) | ((uint32_t)(k + 1) << 10) | (kRankInf << 20);
+                wa[k + 2] = pm[p.h];
+            } else if (npair == 0) {
+                p.wA[k + 2] = pm[p.h];                  // one block only: y[0] = X_0[P_0[h]]
+            }
+        }
+        int R = 4;
+        while (R * 32 < k) R <<= 1;
+        const int gpr = 32 / R, grp = lane / R, sub = lane & (R - 1);
+        const int nw = (k + 31) >> 5;                   // bitset words for ranks < k
+        uint32_t* bw = areaW + lane;                    // word w of this lane at bw[32 w]
+        const uint32_t sentB = (uint32_t)k + 1;
+        for (int bt0 = 0; bt0 < nbt; bt0 += gpr) {
+            const int bt = bt0 + grp;
+            const int boff = bt * k;
+            const bool isB = bt < nbt && warp * bpw + bt >= 1;
+            const int NB = isB ? min(k, tile_n - boff) : 0;
+            const int cs = (NB + R - 1) / R;            // at most 32
+            const int p0 = min(sub * cs, NB), p1 = min(p0 + cs, NB);
+            const uint16_t* pm = permW + (isB ? boff : 0);
+            for (int w = 0; w < nw; ++w) bw[32 * w] = 0u;
+            for (int pos = p0; pos < p1; ++pos) {
+                const int r = rnkW[rix(boff + pos)];
+                bw[32 * (r >> 5)] |= 1u << (r & 31);
+            }
+            // run `sub` starts from the ranks of the group's runs 0 .. sub-1
+            for (int w = 0; w < nw; ++w) {
+                uint32_t v = bw[32 * w];
+                for (int d = 1; d < R; d <<= 1) {
+                    const uint32_t u = __shfl_up_sync(0xffffffffu, v, d, R);
+                    if (sub >= d) v |= u;
+                }
+                const uint32_t ex = __shfl_up_sync(0xffffffffu, v, 1, R);
+                bw[32 * w] = sub == 0 ? 0u : ex;
+            }
+            uint32_t summ = 0;                          // bit w: word w non-empty
+            for (int w = 0; w < nw; ++w) summ |= bw[32 * w] ? (1u << w) : 0u;
+            uint32_t uo[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                uo[i] = 0u;
+                const int pos = p0 + i;
+                if (pos < p1) {
+                    const int r = rnkW[rix(boff + pos)];
+                    const int w = r >> 5, bb = r & 31;
+                    const uint32_t word = bw[32 * w];
+                    const uint32_t mlo = word & ((1u << bb) - 1u);
+                    const uint32_t mhi = word & ~((2u << bb) - 1u);    // bb = 31: 0
+                    const uint32_t slo = summ & ((1u << w) - 1u);
+                    const uint32_t shi = summ & ~((2u << w) - 1u);
+                    const int wlo = slo ? 31 - __clz(slo) : 0;
+                    const int whi = shi ? __ffs(shi) - 1 : 0;
+                    uint32_t xlo = 0u, xhi = 0u;
+                    if (!mlo && slo) xlo = bw[32 * wlo];
+                    if (!mhi && shi) xhi = bw[32 * whi];
+                    const int pred = mlo ? ((w << 5) | (31 - __clz(mlo)))
+                                         : (slo ? ((wlo << 5) | (31 - __clz(xlo))) : -1);
+                    const int succ = mhi ? ((w << 5) | (__ffs(mhi) - 1))
+                                         : (shi ? ((whi << 5) | (__ffs(xhi) - 1)) : -1);
+                    bw[32 * w] = word | (1u << bb);
+                    summ |= 1u << w;
+                    const uint32_t pv = pred >= 0 ? (uint32_t)pm[pred] : sentB;
+                    const uint32_t nx = succ >= 0 ? (uint32_t)pm[succ] : sentB;
+                    uo[i] = nx | (pv << 10);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (p0 + i < p1) areaW[tix(boff + p0 + i)] = uo[i];
+            __syncwarp();
+            // undelete words of this round's blocks
+            const int e0 = bt0 * k, e1 = min(bt0 + gpr, nbt) * k;
+            for (int x = e0 + lane; x < e1 && x < tile_n; x += 32) {
+                const int btx = (int)udiv((uint32_t)x, p.kmagic);
+                const int bx = warp * bpw + btx;
+                if (bx < 1) continue;
+                const int pos = x - btx * k;
+                p.wB[(size_t)(j0 - 1 + bx - 1) * p.kw + pos] =
+                    areaW[tix(x)] | ((uint32_t)jbS[(size_t)(bx - 1) * k + pos] << 20);
+            }
+            __syncwarp();
         }
         return;
     }
