@@ -567,10 +567,58 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
 }
 
 // Fused path (sortlist_kernel wrote the words): construct(A) is a copy of the
-// pair's row of list words (slots 0..k+1, m_A in slot k+2); step i undeletes
-// B's position i with the word wB[i] = make(pb, nb, rb).  Packed format only.
+// pair's row of list words (slots 0..k+1, m_A in slot k+2), made by the lane
+// itself (copy) or beforehand by copy_rows for all the CTA's pairs; step i
+// undeletes B's position i with the word wB[i] = make(pb, nb, rb).  Packed
+// format only.
+//
+// copy_rows: all threads of the CTA copy the rows, 16 bytes at a time and 16
+// loads in flight per thread, into the lanes' bank-private slices.  info[s]
+// describes slot s = pair_off + lane: row address, words (k + 2, 0 for an
+// idle slot), lanes of its warp and the slice's word 0.
+__device__ __forceinline__ void copy_rows(const uint4* info, int nslots, int maxch, uint32_t* words)
+{
+    // chunk-major order: a warp's threads take the same chunk of consecutive
+    // slots, whose words sit in distinct banks
+    const int nthr = blockDim.x, total = nslots * maxch;
+    int c = (int)threadIdx.x / nslots, s = (int)threadIdx.x - c * nslots;
+    const int dc = nthr / nslots, ds = nthr - dc * nslots;
+    for (int c0 = threadIdx.x; c0 < total; c0 += 16 * nthr) {
+        uint4 v[16];
+        uint32_t dst[16], meta[16];                     // meta: lanes | words of the chunk << 8
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            meta[u] = 0u;
+            dst[u] = 0u;
+            v[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (c0 + u * nthr < total) {
+                const uint4 in = info[s];
+                const int nw = (int)(in.z & 0xffffu);
+                if (4 * c < nw) {
+                    const uint4* src = reinterpret_cast<const uint4*>(((uint64_t)in.y << 32) | in.x);
+                    const uint32_t nl = in.z >> 16;
+                    v[u] = __ldg(src + c);
+                    dst[u] = in.w + 4u * (uint32_t)c * nl;
+                    meta[u] = nl | (uint32_t)min(4, nw - 4 * c) << 8;
+                }
+            }
+            s += ds;
+            c += dc;
+            if (s >= nslots) { s -= nslots; ++c; }
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const uint32_t nl = meta[u] & 0xffu, cnt = meta[u] >> 8;
+            uint32_t* d = words + dst[u];
+            if (cnt > 0) d[0] = v[u].x;
+            if (cnt > 1) d[nl] = v[u].y;
+            if (cnt > 2) d[2 * nl] = v[u].z;
+            if (cnt > 3) d[3 * nl] = v[u].w;
+        }
+    }
+}
 __device__ __forceinline__ void chain_body_words(const PipeParams& p, uint32_t* wsl, int lane,
-                                                 int64_t q, uint32_t NL)
+                                                 int64_t q, uint32_t NL, bool copy)
 {
     using LL = Lists<true>;
     const int k = p.k, h = p.h;
@@ -579,20 +627,22 @@ __device__ __forceinline__ void chain_body_words(const PipeParams& p, uint32_t* 
     L.w = wsl + lane;
     L.jr16 = nullptr;
     L.NL = NL;
-    // 16 loads of 16 bytes in flight per lane, then their stores
-    const uint4* wa4 = reinterpret_cast<const uint4*>(p.wA + (size_t)q * p.kw);
-    const int nrec = (k + 2 + 3) >> 2;
-    for (int c0 = 0; c0 < nrec; c0 += 16) {
-        uint4 v[16];
+    if (copy) {
+        // slots 0 .. k+1 by this lane: 16 loads of 16 bytes in flight, then their stores
+        const uint4* wa4 = reinterpret_cast<const uint4*>(p.wA + (size_t)q * p.kw);
+        const int nrec = (k + 2 + 3) >> 2;
+        for (int c0 = 0; c0 < nrec; c0 += 16) {
+            uint4 v[16];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) v[u] = c0 + u < nrec ? __ldg(wa4 + c0 + u) : make_uint4(0, 0, 0, 0);
+            for (int u = 0; u < 16; ++u) v[u] = c0 + u < nrec ? __ldg(wa4 + c0 + u) : make_uint4(0, 0, 0, 0);
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const uint32_t vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+            for (int u = 0; u < 16; ++u) {
+                const uint32_t vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int e = 4 * (c0 + u) + t;
-                if (e < k + 2) L.st(e, vv[t]);
+                for (int t = 0; t < 4; ++t) {
+                    const int e = 4 * (c0 + u) + t;
+                    if (e < k + 2) L.st(e, vv[t]);
+                }
             }
         }
     }
@@ -639,6 +689,11 @@ __device__ __forceinline__ void chain_body_words(const PipeParams& p, uint32_t* 
     }
 }
 
+// Classes whose largest k is above this copy the rows with copy_rows (GB300,
+// n = 2^26, k = 1001: chain 1.13 -> 1.02 ms); below it the CTA barrier cost
+// more than it saved (k <= 64 in the 4096-signal batch: 0.70 -> 0.93 ms).
+constexpr int kCoopCopyMinK = 256;
+
 template <bool PACKED, bool WORDS>
 __global__ void __launch_bounds__(kPipeThreads)
 chain_kernel(SegTable tab, ChainPlan cp)
@@ -646,19 +701,47 @@ chain_kernel(SegTable tab, ChainPlan cp)
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // warp w has 1 << ((lanes_log2 >> 3w) & 7) lanes; slices follow each other
+    // warps past nwarps (fused path) only help copy_rows
     int NL = 0, pair_off = 0;
-    for (int w = 0; w <= warp; ++w) {
+    for (int w = 0; w <= warp && w < cp.nwarps; ++w) {
         const int l = 1 << ((cp.lanes_log2 >> (3 * w)) & 7);
         if (w < warp) pair_off += l; else NL = l;
     }
-    if (lane >= NL) return;
     const int64_t item = (int64_t)blockIdx.x * cp.pairs_per_cta + pair_off + lane;
+    uint32_t* wsl = reinterpret_cast<uint32_t*>(smem) + (uint32_t)pair_off * cp.lane_words;
+    if (WORDS && cp.rec_words <= kCoopCopyMinK + 1) {
+        // short rows: each lane copies its own (no CTA barrier)
+        if (lane >= NL || item >= cp.items) return;
+        int64_t q;
+        const PipeParams p = find_signal(tab, kItemChain, item, &q);
+        chain_body_words(p, wsl, lane, q, (uint32_t)NL, true);
+        return;
+    }
+    if (WORDS) {
+        uint4* info = reinterpret_cast<uint4*>(smem + cp.info_off);
+        const bool act = lane < NL && item < cp.items;
+        int64_t q = 0;
+        PipeParams p;
+        if (act) {
+            p = find_signal(tab, kItemChain, item, &q);
+            const uint64_t src = (uint64_t)(uintptr_t)(p.wA + (size_t)q * p.kw);
+            info[pair_off + lane] = make_uint4((uint32_t)src, (uint32_t)(src >> 32),
+                                               (uint32_t)(p.k + 2) | ((uint32_t)NL << 16),
+                                               (uint32_t)pair_off * cp.lane_words + (uint32_t)lane);
+        } else if (lane < NL) {
+            info[pair_off + lane] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncthreads();
+        copy_rows(info, cp.pairs_per_cta, (int)(cp.rec_words + 3) >> 2, reinterpret_cast<uint32_t*>(smem));
+        __syncthreads();
+        if (act) chain_body_words(p, wsl, lane, q, (uint32_t)NL, false);
+        return;
+    }
+    if (lane >= NL) return;
     if (item >= cp.items) return;
     int64_t q;                                          // pair j = q + 1 of its signal
     const PipeParams p = find_signal(tab, kItemChain, item, &q);
-    uint32_t* wsl = reinterpret_cast<uint32_t*>(smem) + (uint32_t)pair_off * cp.lane_words;
-    if (WORDS) chain_body_words(p, wsl, lane, q, (uint32_t)NL);
-    else chain_body<PACKED>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL);
+    chain_body<PACKED>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL);
 }
 
 // ===========================================================================
@@ -810,8 +893,8 @@ static bool chain_plan(int k, ChainPlan* cp, size_t* bytes)
     int nw = 0, pairs = 0;
     cp->lanes_log2 = 0;
     while (nw < kPipeThreads / 32) {
-        int lg = 5;
-        while (lg >= 0 && used + ((uint64_t)1 << lg) * lane_words > budget) --lg;
+        int lg = 5;                                     // (4 words per pair: copy descriptor)
+        while (lg >= 0 && used + ((uint64_t)1 << lg) * lane_words + 4ull * (pairs + (1 << lg) + 1) > budget) --lg;
         if (lg < 0) break;
         cp->lanes_log2 |= (uint32_t)lg << (3 * nw);
         used += ((uint64_t)1 << lg) * lane_words;
@@ -821,7 +904,8 @@ static bool chain_plan(int k, ChainPlan* cp, size_t* bytes)
     }
     cp->nwarps = nw;
     cp->pairs_per_cta = pairs;
-    *bytes = (size_t)used * 4;
+    cp->info_off = (uint32_t)((used * 4 + 15) & ~15ull);
+    *bytes = (size_t)cp->info_off + 16u * (size_t)pairs;
     return nw > 0;
 }
 
@@ -1082,7 +1166,7 @@ static cudaError_t launch_classes(const ClassPlan* cls, const SegTable* tabs, co
         cp.items = tot[c][kItemChain];
         const int64_t grid = (cp.items + cp.pairs_per_cta - 1) / cp.pairs_per_cta;
         if (cls[c].fused)
-            chain_kernel<true, true><<<(unsigned)grid, 32 * cp.nwarps, cls[c].cbytes, stream>>>(tabs[c], cp);
+            chain_kernel<true, true><<<(unsigned)grid, kPipeThreads, cls[c].cbytes, stream>>>(tabs[c], cp);
         else if (cp.packed)
             chain_kernel<true, false><<<(unsigned)grid, 32 * cp.nwarps, cls[c].cbytes, stream>>>(tabs[c], cp);
         else
