@@ -482,7 +482,7 @@ __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>
 
 template <bool PACKED>
 __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, int lane, int64_t q,
-                                           uint32_t rec_words, uint32_t NL)
+                                           uint32_t rec_words, uint32_t NL, bool copy)
 {
     using LL = Lists<PACKED>;
     const int k = p.k, h = p.h;
@@ -497,7 +497,7 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
     const size_t bbase = (size_t)(q + 1) * p.kp;
     const uint4* sl4 = reinterpret_cast<const uint4*>(p.slink + abase);
     const uint4* ja4 = reinterpret_cast<const uint4*>(p.ja + abase);
-    const int nchunk = p.kp >> 3;
+    const int nchunk = copy ? p.kp >> 3 : 0;            // else copy_lists built slots 0 .. k-1
 #pragma unroll 4
     for (int c = 0; c < nchunk; ++c) {
         const uint4 s0 = __ldg(sl4 + 2 * c), s1 = __ldg(sl4 + 2 * c + 1), jv = __ldg(ja4 + c);
@@ -689,6 +689,66 @@ __device__ __forceinline__ void chain_body_words(const PipeParams& p, uint32_t* 
     }
 }
 
+// copy_lists: construct(A) of the four-kernel path for all the CTA's pairs at
+// once, slots 0 .. k-1 from the sorted-order links (prev:16 | next:16) and
+// joint ranks of block A, 8 slots per chunk, chunk-major like copy_rows.
+// info[2s] = slink row, ja row; info[2s+1] = k (0: idle) | lanes << 16, the
+// slice's word 0, the slice's rank word 0.
+template <bool PACKED>
+__device__ __forceinline__ void copy_lists(const uint4* info, int nslots, int maxch, uint32_t* words)
+{
+    using LL = Lists<PACKED>;
+    const int nthr = blockDim.x, total = nslots * maxch;
+    int c = (int)threadIdx.x / nslots, s = (int)threadIdx.x - c * nslots;
+    const int dc = nthr / nslots, ds = nthr - dc * nslots;
+    for (int c0 = threadIdx.x; c0 < total; c0 += 8 * nthr) {
+        uint4 a[8], b[8], r[8];
+        uint32_t cnt[8], nl[8], dw[8], dr[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            cnt[u] = 0u; nl[u] = 0u; dw[u] = 0u; dr[u] = 0u;
+            a[u] = b[u] = r[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (c0 + u * nthr < total) {
+                const uint4 d = info[2 * s + 1];
+                const int k = (int)(d.x & 0xffffu);
+                if (8 * c < k) {
+                    const uint4 rows = info[2 * s];
+                    const uint4* sl4 = reinterpret_cast<const uint4*>(((uint64_t)rows.y << 32) | rows.x);
+                    const uint4* ja4 = reinterpret_cast<const uint4*>(((uint64_t)rows.w << 32) | rows.z);
+                    a[u] = __ldg(sl4 + 2 * c);
+                    b[u] = __ldg(sl4 + 2 * c + 1);
+                    r[u] = __ldg(ja4 + c);
+                    cnt[u] = (uint32_t)min(8, k - 8 * c);
+                    nl[u] = d.x >> 16;
+                    dw[u] = d.y + 8u * (uint32_t)c * nl[u];
+                    dr[u] = d.z + 4u * (uint32_t)c * nl[u];
+                }
+            }
+            s += ds;
+            c += dc;
+            if (s >= nslots) { s -= nslots; ++c; }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t sv[8] = {a[u].x, a[u].y, a[u].z, a[u].w, b[u].x, b[u].y, b[u].z, b[u].w};
+            const uint32_t jw[4] = {r[u].x, r[u].y, r[u].z, r[u].w};
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                if ((uint32_t)t < cnt[u]) {
+                    const uint32_t rk = t & 1 ? jw[t >> 1] >> 16 : jw[t >> 1] & 0xffffu;
+                    words[dw[u] + (uint32_t)t * nl[u]] = LL::make(sv[t] >> 16, sv[t] & 0xffffu, rk);
+                }
+            }
+            if (!PACKED) {
+                // rank words: two slots each; word j holds slots 2j, 2j+1 of the chunk
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if ((uint32_t)(2 * j) < cnt[u]) words[dr[u] + (uint32_t)j * nl[u]] = jw[j];
+            }
+        }
+    }
+}
+
 // Classes whose largest k is above this copy the rows with copy_rows (GB300,
 // n = 2^26, k = 1001: chain 1.13 -> 1.02 ms); below it the CTA barrier cost
 // more than it saved (k <= 64 in the 4096-signal batch: 0.70 -> 0.93 ms).
@@ -709,7 +769,7 @@ chain_kernel(SegTable tab, ChainPlan cp)
     }
     const int64_t item = (int64_t)blockIdx.x * cp.pairs_per_cta + pair_off + lane;
     uint32_t* wsl = reinterpret_cast<uint32_t*>(smem) + (uint32_t)pair_off * cp.lane_words;
-    if (WORDS && cp.rec_words <= kCoopCopyMinK + 1) {
+    if (WORDS && cp.rec_words <= kCoopCopyMinK + 2) {
         // short rows: each lane copies its own (no CTA barrier)
         if (lane >= NL || item >= cp.items) return;
         int64_t q;
@@ -737,11 +797,32 @@ chain_kernel(SegTable tab, ChainPlan cp)
         if (act) chain_body_words(p, wsl, lane, q, (uint32_t)NL, false);
         return;
     }
-    if (lane >= NL) return;
-    if (item >= cp.items) return;
-    int64_t q;                                          // pair j = q + 1 of its signal
-    const PipeParams p = find_signal(tab, kItemChain, item, &q);
-    chain_body<PACKED>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL);
+    if (cp.rec_words <= kCoopCopyMinK + 2) {
+        if (lane >= NL || item >= cp.items) return;
+        int64_t q;                                      // pair j = q + 1 of its signal
+        const PipeParams p = find_signal(tab, kItemChain, item, &q);
+        chain_body<PACKED>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL, true);
+        return;
+    }
+    uint4* info = reinterpret_cast<uint4*>(smem + cp.info_off);
+    const bool act = lane < NL && item < cp.items;
+    int64_t q = 0;
+    PipeParams p;
+    if (act) {
+        p = find_signal(tab, kItemChain, item, &q);
+        const uint64_t sl = (uint64_t)(uintptr_t)(p.slink + (size_t)q * p.kp);
+        const uint64_t ja = (uint64_t)(uintptr_t)(p.ja + (size_t)q * p.kp);
+        const uint32_t w0 = (uint32_t)pair_off * cp.lane_words + (uint32_t)lane;
+        info[2 * (pair_off + lane)] = make_uint4((uint32_t)sl, (uint32_t)(sl >> 32), (uint32_t)ja, (uint32_t)(ja >> 32));
+        info[2 * (pair_off + lane) + 1] = make_uint4((uint32_t)p.k | ((uint32_t)NL << 16), w0,
+                                                     w0 + cp.rec_words * (uint32_t)NL, 0u);
+    } else if (lane < NL) {
+        info[2 * (pair_off + lane) + 1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncthreads();
+    copy_lists<PACKED>(info, cp.pairs_per_cta, (int)(cp.rec_words - 2 + 7) >> 3, reinterpret_cast<uint32_t*>(smem));
+    __syncthreads();
+    if (act) chain_body<PACKED>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL, false);
 }
 
 // ===========================================================================
@@ -893,8 +974,8 @@ static bool chain_plan(int k, ChainPlan* cp, size_t* bytes)
     int nw = 0, pairs = 0;
     cp->lanes_log2 = 0;
     while (nw < kPipeThreads / 32) {
-        int lg = 5;                                     // (4 words per pair: copy descriptor)
-        while (lg >= 0 && used + ((uint64_t)1 << lg) * lane_words + 4ull * (pairs + (1 << lg) + 1) > budget) --lg;
+        int lg = 5;                                     // (8 words per pair: copy descriptors)
+        while (lg >= 0 && used + ((uint64_t)1 << lg) * lane_words + 8ull * (pairs + (1 << lg)) + 4 > budget) --lg;
         if (lg < 0) break;
         cp->lanes_log2 |= (uint32_t)lg << (3 * nw);
         used += ((uint64_t)1 << lg) * lane_words;
@@ -905,7 +986,7 @@ static bool chain_plan(int k, ChainPlan* cp, size_t* bytes)
     cp->nwarps = nw;
     cp->pairs_per_cta = pairs;
     cp->info_off = (uint32_t)((used * 4 + 15) & ~15ull);
-    *bytes = (size_t)cp->info_off + 16u * (size_t)pairs;
+    *bytes = (size_t)cp->info_off + 32u * (size_t)pairs;
     return nw > 0;
 }
 
@@ -1168,9 +1249,9 @@ static cudaError_t launch_classes(const ClassPlan* cls, const SegTable* tabs, co
         if (cls[c].fused)
             chain_kernel<true, true><<<(unsigned)grid, kPipeThreads, cls[c].cbytes, stream>>>(tabs[c], cp);
         else if (cp.packed)
-            chain_kernel<true, false><<<(unsigned)grid, 32 * cp.nwarps, cls[c].cbytes, stream>>>(tabs[c], cp);
+            chain_kernel<true, false><<<(unsigned)grid, kPipeThreads, cls[c].cbytes, stream>>>(tabs[c], cp);
         else
-            chain_kernel<false, false><<<(unsigned)grid, 32 * cp.nwarps, cls[c].cbytes, stream>>>(tabs[c], cp);
+            chain_kernel<false, false><<<(unsigned)grid, kPipeThreads, cls[c].cbytes, stream>>>(tabs[c], cp);
         if (stats) stats->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
