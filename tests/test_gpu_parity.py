@@ -107,7 +107,7 @@ def test_float_special_values(handle):
 def test_int32_extremes_and_ties(handle):
     rng = np.random.default_rng(1)
     vals = np.array([-2 ** 31, 2 ** 31 - 1, 0, -1, 1], dtype=np.int32)
-    for k in (3, 63, 1001):
+    for k in (3, 63, 129, 255, 1001):
         check_full(handle, rng.choice(vals, size=30_000), k, f"int extremes k={k}")
     check_full(handle, np.full(10_000, 5, np.int32), 101, "constant")
 
