@@ -347,11 +347,11 @@ unwind_kernel(SegTable tab, UnwindPlan up)
 // ===========================================================================
 // chain_kernel: the post-processing of Section 6.2, one lane per block pair.
 // Shared memory per lane (bank-private, word index x * NL + lane):
-//   rec[0 .. k+1]   prev:16 | next:16 (node numbers = slots, see top)
-//   jr [0 .. k+1]   joint rank of the node's current element (u16, two per word)
-// Besides m, each list caches in registers prev(m) and next(m) and their
-// ranks, so the moves of a step need no shared-memory load; the loads that
-// refill the caches are not on the step-to-step dependency path.
+//   rec[0 .. k+1]   the list word of every node (node numbers = slots, see top)
+//   jr [0 .. k+1]   wide format only: joint rank of the node's current element
+//                   (u16, two per word)
+// Each list keeps m, m's word and m's rank in registers (patched in place
+// when a relink touches m), so a step loads only the words m moves to.
 // ===========================================================================
 // Per-lane view of the lists in shared memory.  Slot e's word sits at word
 // index e * NL + lane of the warp's slice, so every lane owns one bank.
