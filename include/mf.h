@@ -170,6 +170,17 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
 mf_status mf_filter_backward(mf_handle h, const float* gy, const int32_t* argmed,
                              int64_t n, int32_t k, float* gx);
 
+/* mf_filter_backward for `rows` independent signals of the same n and k in
+ * one launch (the backward pass of a batched call on equal rows).
+ *  gy      device pointer, rows x (n-k+1) float32, row-major
+ *  argmed  device pointer, rows x (n-k+1) int32, each row's indices local to
+ *          that row (as mf_filter_batched reports them)
+ *  gx      device pointer, rows x n float32 (output, overwritten)
+ * Row r of gx is mf_filter_backward of row r of gy and argmed, bit for bit.
+ * Errors: as mf_filter_backward; rows < 1 is MF_ERR_BAD_N. */
+mf_status mf_filter_backward_rows(mf_handle h, const float* gy, const int32_t* argmed,
+                                  int64_t rows, int64_t n, int32_t k, float* gx);
+
 /* The median filter of mf_filter for callers that cannot call cudaMalloc.
  * The paper has no counterpart: this entry point exists because some callers
  * may not allocate device memory -- code that runs while a stream is being

@@ -69,6 +69,7 @@ def load_library(path: str = LIB_PATH):
             "mf_filter_rank": ([vp, c.c_int, vp, i64, i32, i32, vp, vp], c.c_int),
             "mf_filter_batched": ([vp, c.c_int, vp, vp, vp, i32, vp], c.c_int),
             "mf_filter_backward": ([vp, vp, vp, i64, i32, vp], c.c_int),
+            "mf_filter_backward_rows": ([vp, vp, vp, i64, i64, i32, vp], c.c_int),
             "mf_filter_noalloc": ([c.c_int, vp, i64, i32, vp, vp, vp], c.c_int),
             "mf_sync": ([vp], c.c_int),
             "mf_launch_count": ([vp, c.POINTER(c.c_uint64)], c.c_int),
@@ -201,6 +202,14 @@ def mf_filter_backward(handle, gy, argmed, n: int, k: int, gx):
     _check(load_library().mf_filter_backward(handle, _dptr(gy, "gy"), _dptr(argmed, "argmed"),
                                              int(n), int(k), _dptr(gx, "gx")),
            "mf_filter_backward")
+
+
+def mf_filter_backward_rows(handle, gy, argmed, rows: int, n: int, k: int, gx):
+    """mf_filter_backward of ``rows`` equal-length rows in one launch
+    (row-major gy / argmed of rows x (n-k+1), gx of rows x n)."""
+    _check(load_library().mf_filter_backward_rows(handle, _dptr(gy, "gy"), _dptr(argmed, "argmed"),
+                                                  int(rows), int(n), int(k), _dptr(gx, "gx")),
+           "mf_filter_backward_rows")
 
 
 def mf_filter_noalloc(x, k: int, y, argmed=None, stream=None):

@@ -17,7 +17,7 @@ import numpy as np
 import torch
 
 from . import (default_handle, make_segments, mf_filter, mf_filter_backward,
-               mf_filter_batched, mf_set_stream)
+               mf_filter_backward_rows, mf_filter_batched, mf_set_stream)
 
 
 def _forward(x: torch.Tensor, k: int):
@@ -64,9 +64,7 @@ class MedianFilterFn(torch.autograd.Function):
         if len(ctx.shape) == 1:
             mf_filter_backward(h, gy, a, ctx.shape[0], k, gx)
         else:
-            n = ctx.shape[1]
-            for r in range(ctx.shape[0]):
-                mf_filter_backward(h, gy[r], a[r], n, k, gx[r])
+            mf_filter_backward_rows(h, gy, a.contiguous(), ctx.shape[0], ctx.shape[1], k, gx)
         return gx, None
 
 

@@ -433,21 +433,26 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
     return MF_OK;
 }
 
-mf_status mf_filter_backward(mf_handle h, const float* gy, const int32_t* argmed,
-                             int64_t n, int32_t k, float* gx) {
+mf_status mf_filter_backward_rows(mf_handle h, const float* gy, const int32_t* argmed,
+                                  int64_t rows, int64_t n, int32_t k, float* gx) {
     if (!h || !gy || !argmed || !gx) return MF_ERR_NULL;
-    if (n < 1 || n > (int64_t)INT32_MAX) return MF_ERR_BAD_N;
+    if (rows < 1 || n < 1 || n > (int64_t)INT32_MAX) return MF_ERR_BAD_N;
     if (k < 1) return MF_ERR_K_GT_N;
     if (k % 2 == 0) return MF_ERR_EVEN_K;
     if ((int64_t)k > n) return MF_ERR_K_GT_N;
     const size_t m = (size_t)(n - k + 1);
-    if (overlaps(gx, 4 * (size_t)n, gy, 4 * m) || overlaps(gx, 4 * (size_t)n, argmed, 4 * m))
-        return MF_ERR_OVERLAP;
+    const size_t gxb = 4 * (size_t)n * (size_t)rows, inb = 4 * m * (size_t)rows;
+    if (overlaps(gx, gxb, gy, inb) || overlaps(gx, gxb, argmed, inb)) return MF_ERR_OVERLAP;
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
-    cudaError_t e = mf::launch_backward(gy, argmed, n, k, gx, h->stream, &h->stats.launches);
+    cudaError_t e = mf::launch_backward(gy, argmed, rows, n, k, gx, h->stream, &h->stats.launches);
     if (e == cudaErrorInvalidValue) return MF_ERR_UNSUPPORTED;
     return cuda_status(e);
+}
+
+mf_status mf_filter_backward(mf_handle h, const float* gy, const int32_t* argmed,
+                             int64_t n, int32_t k, float* gx) {
+    return mf_filter_backward_rows(h, gy, argmed, 1, n, k, gx);
 }
 
 mf_status mf_sync(mf_handle h) {

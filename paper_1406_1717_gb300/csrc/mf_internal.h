@@ -132,7 +132,7 @@ cudaError_t launch_large(const void* x, int64_t n, int k, int rank, Elem el, voi
                          LaunchStats* stats);
 
 cudaError_t backward_setup();
-cudaError_t launch_backward(const float* gy, const int32_t* argmed, int64_t n, int k,
+cudaError_t launch_backward(const float* gy, const int32_t* argmed, int64_t rows, int64_t n, int k,
                             float* gx, cudaStream_t stream, uint64_t* launches);
 
 }  // namespace mf

@@ -56,6 +56,7 @@ def test_null_handle_rejected_without_cuda(lib):
     assert lib.mf_filter_host(None, 0, vp(16), 10, 3, vp(64), None) == 1
     assert lib.mf_filter_batched(None, 0, vp(16), vp(64), vp(128), 1, None) == 1
     assert lib.mf_filter_backward(None, vp(16), vp(32), 10, 3, vp(64)) == 1
+    assert lib.mf_filter_backward_rows(None, vp(16), vp(32), 2, 10, 3, vp(64)) == 1
     assert lib.mf_sync(None) == 1
     assert lib.mf_destroy(None) == 1
     assert lib.mf_set_stream(None, None) == 1

@@ -243,6 +243,27 @@ def test_backward_matches_oracle_gradient(handle):
     np.testing.assert_array_less(np.abs(gx.cpu().numpy() - ref), k * 6e-8 * absref + 1e-30)
 
 
+def test_backward_rows_equals_rows_one_by_one(handle):
+    """One launch over equal rows gives each row's single-row result, bit for bit."""
+    rng = np.random.default_rng(4)
+    for rows, n, k in ((5, 3001, 31), (3, 1000, 1), (2, 700, 699)):
+        m = n - k + 1
+        a = np.stack([np.minimum(np.arange(m) + rng.integers(0, k, m), n - 1) for _ in range(rows)])
+        g = rng.standard_normal((rows, m)).astype(np.float32)
+        ad = torch.from_numpy(a.astype(np.int32)).to(DEV)
+        gy = torch.from_numpy(g).to(DEV)
+        gx = torch.full((rows, n), np.nan, device=DEV)
+        mf.mf_filter_backward_rows(handle, gy, ad, rows, n, k, gx)
+        one = torch.full((rows, n), np.nan, device=DEV)
+        for r in range(rows):
+            mf.mf_filter_backward(handle, gy[r], ad[r], n, k, one[r])
+        mf.mf_sync(handle)
+        assert np.array_equal(gx.cpu().numpy().view(np.uint32), one.cpu().numpy().view(np.uint32))
+        ref = np.stack([oracle.median_gradient(g[r].astype(np.float64), a[r], n) for r in range(rows)])
+        bound = np.stack([oracle.median_gradient(np.abs(g[r]).astype(np.float64), a[r], n) for r in range(rows)])
+        assert np.all(np.abs(gx.cpu().numpy() - ref) <= k * 6e-8 * bound + 1e-30)
+
+
 @pytest.mark.parametrize("n,k,kind", [(5_000_000, 1001, "walk"), (3_000_011, 20001, "int"),
                                       (2_500_000, 31, "walk64")])
 def test_host_entry_point_chunked(handle, n, k, kind):
