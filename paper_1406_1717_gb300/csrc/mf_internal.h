@@ -63,10 +63,11 @@ struct UnwindPlan {
 // tiles), merges the pairs and makes B's unwind links; the chain kernel reads
 // its list words.  Packed chain format only (slots fit in 10 bits).
 constexpr int kFusedMaxK = 1021;
+constexpr int kMidMaxK = 4093;                   // 12-bit slot numbers: slots 0 .. k+1 <= 4094
 constexpr int kTileElems = 1024;                 // elements per warp tile
 constexpr int kSortListWarps = 8;          // warps (tiles) per sortlist CTA
 struct ChainPlan {
-    bool packed;              // one 32-bit word per list node (k <= 1021)
+    int fmt;                  // list node format: packed (k <= 1021), mid (k <= kMidMaxK), wide
     int nwarps;
     int pairs_per_cta;
     uint32_t lanes_log2;      // 3 bits per warp: warp w handles 1 << field pairs

@@ -355,43 +355,59 @@ unwind_kernel(SegTable tab, UnwindPlan up)
 // ===========================================================================
 // Per-lane view of the lists in shared memory.  Slot e's word sits at word
 // index e * NL + lane of the warp's slice, so every lane owns one bank.
-//   PACKED (k <= 1021): next:10 | prev:10 | joint rank:11 in one word
+//   packed (k <= 1021): next:10 | prev:10 | joint rank:11 in one word
+//   mid    (k <= 4093): next:12 | prev:12 | joint rank bits 12..5 in one word,
+//                       rank bits 4..0 in a byte array (5 bytes per node)
 //   wide             : next:16 | prev:16, joint rank in a separate u16 array
+// The side arrays are bank-private too: the 4 bytes or 2 halves of the word
+// at word index (e / 4 or e / 2) * NL + lane.
 // Relinks never read the word: when delete(A, i) unlinks i, next(prev(i)) is
 // i and prev(next(i)) is i; when undelete(B, i) relinks i between p and n,
-// next(p) is n and prev(n) is p.  So in the packed format each relink is one
-// XOR of old ^ new into the field; in the wide format it is a 16-bit store
-// (equations del / undo-del of Section 4).
-template <bool PACKED>
+// next(p) is n and prev(n) is p.  So in the packed and mid formats each
+// relink is one XOR of old ^ new into the field; in the wide format it is a
+// 16-bit store (equations del / undo-del of Section 4).
+enum { kFmtPacked = 0, kFmtMid = 1, kFmtWide = 2 };
+
+template <int FMT>
 struct Lists {
-    static constexpr int PSH = PACKED ? 10 : 16;
-    static constexpr uint32_t FM = PACKED ? 0x3ffu : 0xffffu;
-    static constexpr uint32_t RINF = PACKED ? 0x7ffu : 0xffffu;
+    static constexpr bool PACKED = FMT == kFmtPacked, MID = FMT == kFmtMid;
+    static constexpr int PSH = PACKED ? 10 : (MID ? 12 : 16);
+    static constexpr uint32_t FM = (1u << PSH) - 1u;
+    static constexpr uint32_t RINF = PACKED ? 0x7ffu : (MID ? 0x1fffu : 0xffffu);
     uint32_t* w;              // this lane's word 0
     uint16_t* jr16;           // wide format: this lane's rank array
+    uint8_t* jr8;             // mid format: this lane's array of rank bits 4..0
     uint32_t NL;              // lanes of this warp: slot e's word is w[e * NL]
     __device__ __forceinline__ uint32_t ld(uint32_t e) const { return w[e * NL]; }
     __device__ __forceinline__ void st(uint32_t e, uint32_t v) const { w[e * NL] = v; }
     __device__ __forceinline__ void xr(uint32_t e, uint32_t v) const { atomicXor(&w[e * NL], v); }
     // relinks: next(e) <- v (old value `old`), prev(e) <- v
     __device__ __forceinline__ void set_next(uint32_t e, uint32_t v, uint32_t old) const {
-        if (PACKED) xr(e, v ^ old);
+        if (PACKED || MID) xr(e, v ^ old);
         else reinterpret_cast<uint16_t*>(w)[e * 2 * NL] = (uint16_t)v;
     }
     __device__ __forceinline__ void set_prev(uint32_t e, uint32_t v, uint32_t old) const {
-        if (PACKED) xr(e, (v ^ old) << PSH);
+        if (PACKED || MID) xr(e, (v ^ old) << PSH);
         else reinterpret_cast<uint16_t*>(w)[e * 2 * NL + 1] = (uint16_t)v;
     }
     __device__ __forceinline__ uint16_t& JR(uint32_t e) const { return jr16[(e >> 1) * 2 * NL + (e & 1)]; }
+    __device__ __forceinline__ uint8_t& JB(uint32_t e) const { return jr8[(e >> 2) * 4 * NL + (e & 3)]; }
     __device__ __forceinline__ static uint32_t nxt(uint32_t v) { return v & FM; }
     __device__ __forceinline__ static uint32_t prv(uint32_t v) { return (v >> PSH) & FM; }
     // rank of slot e whose word is v
     __device__ __forceinline__ uint32_t rank(uint32_t e, uint32_t v) const {
         if (PACKED) return v >> 20;
+        if (MID) return ((v >> 24) << 5) | (uint32_t)JB(e);
         return JR(e);
     }
+    // the part of slot e's rank that is not in its word (mid, wide)
+    __device__ __forceinline__ void set_rank(uint32_t e, uint32_t r) const {
+        if (MID) JB(e) = (uint8_t)(r & 31u);
+        else if (!PACKED) JR(e) = (uint16_t)r;
+    }
     __device__ __forceinline__ static uint32_t make(uint32_t prev, uint32_t next, uint32_t r) {
-        return PACKED ? (next | (prev << 10) | (r << 20)) : (next | (prev << 16));
+        return PACKED ? (next | (prev << 10) | (r << 20))
+                      : (MID ? (next | (prev << 12) | ((r >> 5) << 24)) : (next | (prev << 16)));
     }
 };
 
@@ -409,12 +425,13 @@ struct PairState {
 // step's last store); the next step's word is loaded into *wnext.  B's
 // position i comes back with the links pb / nb that unwind(B) left it and
 // joint rank rb; wbw is its list word make(pb, nb, rb).
-template <bool PACKED>
-__device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>& L, uint32_t i,
+template <int FMT>
+__device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<FMT>& L, uint32_t i,
                                               uint32_t wa, uint32_t pb, uint32_t nb, uint32_t rb,
                                               uint32_t wbw, uint32_t* wnext)
 {
-    using LL = Lists<PACKED>;
+    using LL = Lists<FMT>;
+    constexpr bool PACKED = LL::PACKED;
     // -------- delete(A, i) ----------------------------------------------------
     const uint32_t pa = LL::prv(wa), na = LL::nxt(wa);
     const uint32_t ra = L.rank(i, wa);
@@ -439,7 +456,7 @@ __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>
     st.sA -= (small || sApos) ? 1 : 0;                  // s <- max(0, s - 1)
     // -------- undelete(B, i) ----------------------------------------------------
     L.st(i, wbw);                                       // wbw = make(pb, nb, rb)
-    if (!PACKED) L.JR(i) = (uint16_t)rb;
+    if (!PACKED) L.set_rank(i, rb);
     L.set_next(pb, i, nb);                              // next[prev[i]] <- i
     L.set_prev(nb, i, pb);                              // prev[next[i]] <- i
     st.wmB ^= (pb == st.mB) ? (nb ^ i) : 0u;
@@ -480,16 +497,18 @@ __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<PACKED>
     return st.rmA < st.rmB ? st.mA : (0x8000u | st.mB);
 }
 
-template <bool PACKED>
+template <int FMT>
 __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, int lane, int64_t q,
                                            uint32_t rec_words, uint32_t NL, bool copy)
 {
-    using LL = Lists<PACKED>;
+    using LL = Lists<FMT>;
+    constexpr bool PACKED = LL::PACKED;
     const int k = p.k, h = p.h;
     const int NB = (int)min((int64_t)k, p.n - (q + 1) * (int64_t)k);
     LL L;
     L.w = wsl + lane;
     L.jr16 = reinterpret_cast<uint16_t*>(wsl + rec_words * NL + lane);
+    L.jr8 = reinterpret_cast<uint8_t*>(wsl + rec_words * NL + lane);
     L.NL = NL;
 
     // ---- construct(A) in slot space + empty B (rows of kp elements) ----------
@@ -509,7 +528,7 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
             if (e < k) {
                 const uint32_t r = t & 1 ? jw[t >> 1] >> 16 : jw[t >> 1] & 0xffffu;
                 L.st(e, LL::make(sv[t] >> 16, sv[t] & 0xffffu, r));
-                if (!PACKED) L.JR(e) = (uint16_t)r;
+                if (!PACKED) L.set_rank(e, r);
             }
         }
     }
@@ -517,7 +536,7 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
     const uint16_t* permA = p.perm + abase;                     // block j-1 = q
     L.st(SA, LL::make(__ldg(permA + k - 1), __ldg(permA), LL::RINF));
     L.st(SB, LL::make(SB, SB, LL::RINF));
-    if (!PACKED) { L.JR(SA) = (uint16_t)LL::RINF; L.JR(SB) = (uint16_t)LL::RINF; }
+    if (!PACKED) { L.set_rank(SA, LL::RINF); L.set_rank(SB, LL::RINF); }
 
     PairState st;
     st.mA = __ldg(permA + h);
@@ -554,7 +573,7 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
                 const uint32_t rb = t & 1 ? jw[t >> 1] >> 16 : jw[t >> 1] & 0xffffu;
                 uint32_t wn;
                 const uint32_t pb = wbv[t] >> 16, nb = wbv[t] & 0xffffu;
-                const uint32_t o = pair_step<PACKED>(st, L, (uint32_t)i, wa, pb, nb, rb,
+                const uint32_t o = pair_step<FMT>(st, L, (uint32_t)i, wa, pb, nb, rb,
                                                      LL::make(pb, nb, rb), &wn);
                 wa = wn;
                 ov[t >> 1] |= (t & 1) ? (o << 16) : o;
@@ -620,7 +639,7 @@ __device__ __forceinline__ void copy_rows(const uint4* info, int nslots, int max
 __device__ __forceinline__ void chain_body_words(const PipeParams& p, uint32_t* wsl, int lane,
                                                  int64_t q, uint32_t NL, bool copy)
 {
-    using LL = Lists<true>;
+    using LL = Lists<kFmtPacked>;
     const int k = p.k, h = p.h;
     const int NB = (int)min((int64_t)k, p.n - (q + 1) * (int64_t)k);
     LL L;
@@ -677,7 +696,7 @@ __device__ __forceinline__ void chain_body_words(const PipeParams& p, uint32_t* 
             if (i < NB) {
                 const uint32_t w = wbv[t];
                 uint32_t wn;
-                const uint32_t o = pair_step<true>(st, L, (uint32_t)i, wa, LL::prv(w), LL::nxt(w),
+                const uint32_t o = pair_step<kFmtPacked>(st, L, (uint32_t)i, wa, LL::prv(w), LL::nxt(w),
                                                    w >> 20, w, &wn);
                 wa = wn;
                 ov[t >> 1] |= (t & 1) ? (o << 16) : o;
@@ -694,10 +713,10 @@ __device__ __forceinline__ void chain_body_words(const PipeParams& p, uint32_t* 
 // joint ranks of block A, 8 slots per chunk, chunk-major like copy_rows.
 // info[2s] = slink row, ja row; info[2s+1] = k (0: idle) | lanes << 16, the
 // slice's word 0, the slice's rank word 0.
-template <bool PACKED>
+template <int FMT>
 __device__ __forceinline__ void copy_lists(const uint4* info, int nslots, int maxch, uint32_t* words)
 {
-    using LL = Lists<PACKED>;
+    using LL = Lists<FMT>;
     const int nthr = blockDim.x, total = nslots * maxch;
     int c = (int)threadIdx.x / nslots, s = (int)threadIdx.x - c * nslots;
     const int dc = nthr / nslots, ds = nthr - dc * nslots;
@@ -721,7 +740,7 @@ __device__ __forceinline__ void copy_lists(const uint4* info, int nslots, int ma
                     cnt[u] = (uint32_t)min(8, k - 8 * c);
                     nl[u] = d.x >> 16;
                     dw[u] = d.y + 8u * (uint32_t)c * nl[u];
-                    dr[u] = d.z + 4u * (uint32_t)c * nl[u];
+                    dr[u] = d.z + (LL::MID ? 2u : 4u) * (uint32_t)c * nl[u];
                 }
             }
             s += ds;
@@ -739,7 +758,16 @@ __device__ __forceinline__ void copy_lists(const uint4* info, int nslots, int ma
                     words[dw[u] + (uint32_t)t * nl[u]] = LL::make(sv[t] >> 16, sv[t] & 0xffffu, rk);
                 }
             }
-            if (!PACKED) {
+            if (LL::MID) {
+                // rank bits 4..0: four slots per word; word j holds slots 4j .. 4j+3 of the chunk
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const uint32_t lo = jw[2 * j], hi = jw[2 * j + 1];
+                    const uint32_t bytes = (lo & 31u) | (((lo >> 16) & 31u) << 8) |
+                                           ((hi & 31u) << 16) | (((hi >> 16) & 31u) << 24);
+                    if ((uint32_t)(4 * j) < cnt[u]) words[dr[u] + (uint32_t)j * nl[u]] = bytes;
+                }
+            } else if (!LL::PACKED) {
                 // rank words: two slots each; word j holds slots 2j, 2j+1 of the chunk
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
@@ -754,7 +782,7 @@ __device__ __forceinline__ void copy_lists(const uint4* info, int nslots, int ma
 // more than it saved (k <= 64 in the 4096-signal batch: 0.70 -> 0.93 ms).
 constexpr int kCoopCopyMinK = 256;
 
-template <bool PACKED, bool WORDS>
+template <int FMT, bool WORDS>
 __global__ void __launch_bounds__(kPipeThreads)
 chain_kernel(SegTable tab, ChainPlan cp)
 {
@@ -801,7 +829,7 @@ chain_kernel(SegTable tab, ChainPlan cp)
         if (lane >= NL || item >= cp.items) return;
         int64_t q;                                      // pair j = q + 1 of its signal
         const PipeParams p = find_signal(tab, kItemChain, item, &q);
-        chain_body<PACKED>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL, true);
+        chain_body<FMT>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL, true);
         return;
     }
     uint4* info = reinterpret_cast<uint4*>(smem + cp.info_off);
@@ -820,9 +848,9 @@ chain_kernel(SegTable tab, ChainPlan cp)
         info[2 * (pair_off + lane) + 1] = make_uint4(0u, 0u, 0u, 0u);
     }
     __syncthreads();
-    copy_lists<PACKED>(info, cp.pairs_per_cta, (int)(cp.rec_words - 2 + 7) >> 3, reinterpret_cast<uint32_t*>(smem));
+    copy_lists<FMT>(info, cp.pairs_per_cta, (int)(cp.rec_words - 2 + 7) >> 3, reinterpret_cast<uint32_t*>(smem));
     __syncthreads();
-    if (act) chain_body<PACKED>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL, false);
+    if (act) chain_body<FMT>(p, wsl, lane, q, cp.rec_words, (uint32_t)NL, false);
 }
 
 // ===========================================================================
@@ -965,9 +993,11 @@ static bool sort_plan(int k, int G, SortPlan* sp, size_t* bytes, bool wide)
 // 1.37 ms against 1.14 ms for one CTA of 57 pairs.
 static bool chain_plan(int k, ChainPlan* cp, size_t* bytes)
 {
-    cp->packed = k <= 1021;
+    cp->fmt = k <= kFusedMaxK ? kFmtPacked : (k <= kMidMaxK ? kFmtMid : kFmtWide);
     cp->rec_words = (uint32_t)(k + 2);
-    const uint32_t lane_words = cp->rec_words + (cp->packed ? 0u : (uint32_t)((k + 3) / 2));
+    const uint32_t side = cp->fmt == kFmtPacked ? 0u
+                        : (cp->fmt == kFmtMid ? (uint32_t)((k + 2 + 3) / 4) : (uint32_t)((k + 3) / 2));
+    const uint32_t lane_words = cp->rec_words + side;
     cp->lane_words = lane_words;
     const uint64_t budget = (uint64_t)kMaxSmemBytes / 4;       // words
     uint64_t used = 0;
@@ -1084,9 +1114,10 @@ cudaError_t pipeline_setup()
     if ((e = cudaFuncSetAttribute(epilogue_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
     if ((e = cudaFuncSetAttribute(unwind_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
     if ((e = cudaFuncSetAttribute(unwind_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
-    if ((e = cudaFuncSetAttribute(chain_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
-    if ((e = cudaFuncSetAttribute(chain_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
-    if ((e = cudaFuncSetAttribute(chain_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(chain_kernel<kFmtPacked, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(chain_kernel<kFmtPacked, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(chain_kernel<kFmtMid, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
+    if ((e = cudaFuncSetAttribute(chain_kernel<kFmtWide, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes))) return e;
     if ((e = sortlist_setup())) return e;
     return cudaFuncSetAttribute(epilogue_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
 }
@@ -1108,9 +1139,9 @@ struct ClassPlan {
 };
 
 // Class boundaries: the packed list format ends at k = 1021, the one-word
-// unwind summary at k = 1024; smaller classes keep the shared-memory layouts
-// of small k.
-static const int kClassMax[] = {64, 256, 1021, 2047, 4095, 1 << 30};
+// unwind summary at k = 1024, the mid list format at k = 4093; smaller
+// classes keep the shared-memory layouts of small k.
+static const int kClassMax[] = {64, 256, 1021, 2047, kMidMaxK, 1 << 30};
 
 // Built-in launch-plan choices per class where a measurement beat the
 // capacity rule (0 = use the rule): on GB300 at k = 1001 (n = 2^26 random
@@ -1247,11 +1278,13 @@ static cudaError_t launch_classes(const ClassPlan* cls, const SegTable* tabs, co
         cp.items = tot[c][kItemChain];
         const int64_t grid = (cp.items + cp.pairs_per_cta - 1) / cp.pairs_per_cta;
         if (cls[c].fused)
-            chain_kernel<true, true><<<(unsigned)grid, kPipeThreads, cls[c].cbytes, stream>>>(tabs[c], cp);
-        else if (cp.packed)
-            chain_kernel<true, false><<<(unsigned)grid, kPipeThreads, cls[c].cbytes, stream>>>(tabs[c], cp);
+            chain_kernel<kFmtPacked, true><<<(unsigned)grid, kPipeThreads, cls[c].cbytes, stream>>>(tabs[c], cp);
+        else if (cp.fmt == kFmtPacked)
+            chain_kernel<kFmtPacked, false><<<(unsigned)grid, kPipeThreads, cls[c].cbytes, stream>>>(tabs[c], cp);
+        else if (cp.fmt == kFmtMid)
+            chain_kernel<kFmtMid, false><<<(unsigned)grid, kPipeThreads, cls[c].cbytes, stream>>>(tabs[c], cp);
         else
-            chain_kernel<false, false><<<(unsigned)grid, kPipeThreads, cls[c].cbytes, stream>>>(tabs[c], cp);
+            chain_kernel<kFmtWide, false><<<(unsigned)grid, kPipeThreads, cls[c].cbytes, stream>>>(tabs[c], cp);
         if (stats) stats->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -1,7 +1,7 @@
 """Autotuner of the launch plans, per window-size class, and of the tier
 crossover.
 
-For each class of k (<= 64, <= 256, <= 1021, <= 2047, <= 4095) the tuner
+For each class of k (<= 64, <= 256, <= 1021, <= 2047, <= 4093) the tuner
 times the candidate numbers of block pairs per CTA of the sort+merge kernel
 and of the store kernel on a seeded random-walk signal, with the library's
 CUDA-event kernel timing (mf_set_timing / mf_kernel_times), and applies the
@@ -23,7 +23,7 @@ import torch
 from . import (mf_filter, mf_kernel_times, mf_set_stream, mf_set_tier_threshold,
                mf_set_timing, mf_set_tuning, mf_sync)
 
-CLASS_K = (63, 255, 1001, 2047, 4095)          # one representative k per class
+CLASS_K = (63, 255, 1001, 2047, 4093)          # one representative k per class
 TIER_K = (2047, 3001, 4095, 5001, 6001, 7001, 8001, 9343)
 PIPELINE_ONLY = 1 << 30                        # threshold capped to the pipeline's limit
 SORT_CANDIDATES = (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64)

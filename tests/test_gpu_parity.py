@@ -63,7 +63,7 @@ def test_small_uniform_k31_full(handle):
 
 
 @pytest.mark.parametrize("k", [1, 3, 5, 31, 33, 63, 65, 127, 129, 255, 341, 511, 513, 1001, 1021, 1023,
-                               1025, 2047, 4095])
+                               1025, 2047, 4093, 4095])
 def test_block_boundary_sizes(handle, k):
     rng = np.random.default_rng(k)
     for n in sorted({k, k + 1, 2 * k - 1, 2 * k, 2 * k + 1, 5 * k, 5 * k + int(rng.integers(1, k + 1)),
@@ -112,7 +112,7 @@ def test_int32_extremes_and_ties(handle):
     check_full(handle, np.full(10_000, 5, np.int32), 101, "constant")
 
 
-@pytest.mark.parametrize("k", [1023, 2047, 3001, 4095])
+@pytest.mark.parametrize("k", [1023, 2047, 3001, 4093, 4095])
 def test_long_block_sort_heavy_ties(handle, k):
     """Five distinct values over blocks long enough that the sort splits each
     block into runs and joins them by merging: equal keys must stay in index

@@ -60,7 +60,7 @@ def signals(n, seed):
     return {"float64": f, "int64": i, "int64_ties": t}
 
 
-@pytest.mark.parametrize("k", [1, 3, 31, 1001, 1025, 4095])
+@pytest.mark.parametrize("k", [1, 3, 31, 1001, 1025, 4093, 4095])
 def test_wide_full(handle, k):
     n = 3 * k + 777
     for name, x in signals(n, k).items():
