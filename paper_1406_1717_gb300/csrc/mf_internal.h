@@ -73,7 +73,7 @@ struct ChainPlan {
     uint32_t lanes_log2;      // 3 bits per warp: warp w handles 1 << field pairs
     uint32_t lane_words;      // shared-memory words per pair
     uint32_t rec_words;       // k + 2
-    uint32_t info_off;        // byte offset of the per-pair copy descriptors (fused path)
+    uint32_t info_off;        // byte offset of the per-pair descriptors of the CTA-wide construct
     int64_t items;            // pairs in the launch
 };
 

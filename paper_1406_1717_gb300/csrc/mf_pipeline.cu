@@ -788,8 +788,8 @@ chain_kernel(SegTable tab, ChainPlan cp)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // warp w has 1 << ((lanes_log2 >> 3w) & 7) lanes; slices follow each other
-    // warps past nwarps (fused path) only help copy_rows
+    // warp w has 1 << ((lanes_log2 >> 3w) & 7) lanes; slices follow each other;
+    // warps past nwarps only help the CTA-wide construct (copy_rows, copy_lists)
     int NL = 0, pair_off = 0;
     for (int w = 0; w <= warp && w < cp.nwarps; ++w) {
         const int l = 1 << ((cp.lanes_log2 >> (3 * w)) & 7);
