@@ -241,3 +241,23 @@ def test_gradient_scatter_matches_finite_differences():
     fd = np.array([(loss(x + eps * np.eye(n)[j]) - loss(x - eps * np.eye(n)[j])) / (2 * eps)
                    for j in range(n)])
     np.testing.assert_allclose(grad, fd, rtol=1e-6, atol=1e-6)
+
+
+def test_batched_packing_against_counting():
+    """oracle.batched: each packed segment filtered on its own, outputs placed at
+    y_off, argmed relative to the segment start -- checked by counting (no sort)
+    on small segments of mixed n and k, with gaps between them in x and y."""
+    rng = np.random.default_rng(11)
+    n = np.array([7, 1, 12, 5, 9])
+    k = np.array([3, 1, 5, 5, 1])
+    x_off = np.array([0, 9, 12, 30, 40])
+    y_total = int((n - k + 1).sum()) + 6
+    y_off = np.array([0, 6, 8, 17, 20])
+    x = rng.integers(-3, 4, size=60).astype(np.int32)
+    y, arg = oracle.batched(x, n, k, x_off, y_off, y_total)
+    for s in range(len(n)):
+        seg = [int(v) for v in x[x_off[s]:x_off[s] + n[s]]]
+        for i in range(n[s] - k[s] + 1):
+            w = seg[i:i + k[s]]
+            assert y[y_off[s] + i] == count_median(w)
+            assert arg[y_off[s] + i] == count_argmedian(w, i)
