@@ -17,8 +17,13 @@
 //                     (Section 4, "Unwind"); one lane per block.
 //   chain_kernel      one lane per pair: delete(A, i), undelete(B, i),
 //                     advance, print min(peek) for every step (Section 6.2),
-//                     lists in shared memory.
+//                     lists in shared memory (built by the whole CTA first
+//                     when k > 256).
 //   epilogue_kernel   node -> input element, coalesced stores of y / argmed.
+//
+// For 4-byte elements and k <= kFusedMaxK, sortlist_kernel (mf_sortlist.cu)
+// replaces the first two kernels and writes the list words themselves; the
+// chain kernel then copies them (chain_body_words).
 //
 // Node numbering ("slots"): node i of the pair's lists is position i of A
 // until step i deletes it, and position i of B from the moment step i
@@ -27,7 +32,8 @@
 // (Section 5.3), shared by A and B.  Comparisons use the joint rank of the
 // node's element (the pi^-1 form of Section 5.2, extended across the pair),
 // so "alpha[i] is small" is jr(i) < jr(m) and peek(A) <= peek(B) is
-// jr(mA) < jr(mB); the sentinels have rank 0xFFFF, above every element.
+// jr(mA) < jr(mB); the sentinels have the largest rank the node format holds
+// (all ones), above every element.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "mf_device.cuh"
