@@ -215,7 +215,7 @@ mf_status mf_sync(mf_handle h);
 mf_status mf_launch_count(mf_handle h, uint64_t* count);
 
 /* Launch-plan tuning for the window-size class that contains k (classes
- * k <= 64, <= 256, <= 1021, <= 2047, <= 4095, larger): block pairs per CTA
+ * k <= 64, <= 256, <= 1021, <= 2047, <= 4093, larger): block pairs per CTA
  * of the sort+merge kernel and of the store kernel (0 = built-in choice;
  * values above the built-in choice, which fills shared memory, are capped).
  * Used by the autotuner in paper_1406_1717_gb300/tune.py. */
