@@ -7,9 +7,11 @@ reference arm may import this package.  The CUDA library in
 ``mf_oracle.c`` is the plain definition (paper Section 1: y_i is the median of
 x_i .. x_{i+k-1}; Section 2: find the median of every window separately),
 compiled with gcc into ``oracle/_build/liboracle.so`` on first use.
-``paper_method.py`` restates the paper's own algorithm (Sections 3-6) for the
-invariant and case-table tests; it is not used to produce expected values
-for the CUDA path.
+``paper_method.py`` is a set-level model of the paper's method, written from
+its definitions (the block interface of Section 5, the list equations of
+Section 4, the post-processing steps of Section 6.2), for the invariant and
+case-table tests; it is not used to produce expected values for the CUDA
+path.
 
 Parity pins: every function here is checked in ``tests/test_oracle_pins.py``
 against brute force, closed forms, library routines (numpy / scipy), the

@@ -1,180 +1,178 @@
-"""The paper's own median-filter algorithm on the CPU -- TEST INFRASTRUCTURE ONLY.
+"""A set-level model of the paper's median-filter method -- TEST INFRASTRUCTURE ONLY.
 
-Restates, for the tests, the two-phase method of "Median Filtering is
-Equivalent to Sorting" (Suomela):
+Only the tests import this module; no product code does, and it never
+supplies expected values to the CUDA path (those come from the plain
+definition in ``mf_oracle.c``).  It exists to pin the reasoning behind the
+method, written from the paper's definitions rather than from its printed
+code:
 
-* Section 3 / Section 6.1 -- piecewise stable sort: each block X_j of length
-  k = 2h + 1 gets the permutation P_j that sorts the pairs (X_j[i], i).
-* Section 5 -- the block data structure: a sorted doubly-linked list over the
-  block's indices with a sentinel node k, arrays prev/next of length k + 1,
-  a counter s of "small" elements and a pointer m to the first large one
-  (Section 5.3 invariants: next[k] = p_0, prev[k] = p_{c-1}, m = p_s).
-  Operations construct / delete / undelete / unwind / advance / small / peek
-  (Figures "Block data structure interface" and "... implementation").
-* Section 6.2 -- post-processing: for each adjacent pair of blocks, delete
-  the old block's elements in index order while undoing the new block's
-  deletions (Knuth's dancing links, Section 4 equations del / undo-del),
-  advance one pointer whenever s_A + s_B < h, and print min(peek A, peek B).
+* Section 5 defines a block data structure as a tuple (alpha, pi, L, s): a
+  block of input, the permutation that sorts it, a list L holding a subset of
+  the block in sorted order, and a counter s; the first s elements of L are
+  "small", the rest "large".  The interface (Fig. block-if) fixes what each
+  operation does to (L, s):
+    construct  L = every element, s = h
+    delete     remove alpha[i] from L, then s = max(0, s - 1)
+    undelete   put alpha[i] back into L (s unchanged); deletions and
+               undeletions must be properly nested (Section 5.1)
+    unwind     delete(k-1), ..., delete(0)
+    advance    s = s + 1
+    small      s
+    peek       the first large element, or +inf when every element is small
+  ``RankBlock`` keeps exactly that: L as the sorted list of the live
+  elements' ranks in the stable order of the block, and s.  Section 5.2's
+  remark that pi^-1 may replace the pairs (alpha[i], i) in comparisons is
+  what makes ranks a faithful stand-in for the values.
+* Section 4 defines the two list updates behind delete and undelete
+  (equations del and undo-del, Knuth's dancing links).  ``DancingLinks``
+  applies them to prev / next arrays with a sentinel node, and is used to
+  pin the two facts the GPU path builds on: properly nested undeletions
+  restore the list exactly, and after unwind every node still holds the
+  neighbours it had when it was deleted (the unwind links).
+* Section 6.2 (Fig. postprocess) combines the blocks; ``sort_median`` runs
+  those steps on ``RankBlock`` states and records the sets S_A, S_B, L_A, L_B
+  around every step, so the tests can check the invariant of Section 6.3
+  (eq. inv) and the rows of the case-analysis table of Lemma 1.
 
 Readings of the paper used here (each also listed in the design notes):
-* unwind: the implementation figure prints the *undelete* formulas inside
-  unwind; the interface figure defines unwind as delete(k-1), ..., delete(0),
-  so this file unlinks with the deletion formulas and then sets m = k, s = 0.
 * n not a multiple of k: the last block has r = n - (b-1) k elements and its
-  pair emits r outputs (the paper calls the extension "straightforward").
-* Ties: the stable sort orders equal values by index inside a block, and
-  peek(A) <= peek(B) advances A, so equal values of the older block count as
-  smaller (Section 6.3).
-
-It is used to pin the invariant of Section 6.3 (s_A + s_B = h and
-S_A u S_B = H_AB before every output), the seven cases of the case-analysis
-table, and properly nested delete/undelete.  Expected values for the CUDA
-path always come from the plain definition in ``mf_oracle.c``.
+  pair prints r outputs (the paper calls the extension "straightforward").
+* Ties: blocks are sorted stably, and peek(A) <= peek(B) advances and prints
+  A, so on equal values the older block counts as smaller (Section 6.3).
 """
 from __future__ import annotations
 
+import bisect
 import math
 
 
-class SortedBlock:
-    """One block data structure B = (alpha, pi, L, s) of Section 4."""
+def stable_order(alpha):
+    """pi: positions of the block in the order of the pairs (alpha[i], i)
+    (Section 5.2), and pi^-1: the rank of every position."""
+    pi = sorted(range(len(alpha)), key=lambda i: (alpha[i], i))
+    inv = [0] * len(alpha)
+    for r, p in enumerate(pi):
+        inv[p] = r
+    return pi, inv
+
+
+class RankBlock:
+    """(alpha, pi, L, s) of Section 5 with L kept as sorted ranks."""
 
     def __init__(self, alpha, h: int):
-        # construct(alpha, pi): L holds every element in sorted order, s = h.
         self.alpha = list(alpha)
-        self.size = len(self.alpha)
         self.h = h
-        self.sentinel = self.size                      # node k
-        self.pi = sorted(range(self.size), key=lambda i: (self.alpha[i], i))
-        self.prev = [0] * (self.size + 1)
-        self.next = [0] * (self.size + 1)
-        order = [self.sentinel] + self.pi + [self.sentinel]
-        for left, right in zip(order[:-1], order[1:]):
-            self.next[left] = right
-            self.prev[right] = left
-        self.s = h
-        self.m = self.pi[h] if h < self.size else self.sentinel
+        self.pi, self.rank = stable_order(self.alpha)
+        self.live = list(range(len(self.alpha)))   # construct: every element ...
+        self.s = min(h, len(self.live))            # ... and the first h are small
+        self._removed = []                         # stack of deleted positions
 
-    # -- queries ----------------------------------------------------------
-    def at_end(self) -> bool:
-        return self.m == self.sentinel
-
-    def peek(self):
-        """First large element's value, or +inf if every element is small."""
-        return math.inf if self.at_end() else self.alpha[self.m]
-
+    # -- the interface's queries ---------------------------------------------
     def small(self) -> int:
         return self.s
 
-    def is_small(self, i: int) -> bool:
-        """alpha[i] is small iff (alpha[i], i) < (alpha[m], m); alpha[k] = +inf."""
-        if self.at_end():
-            return True
-        return (self.alpha[i], i) < (self.alpha[self.m], self.m)
+    def first_large(self):
+        """Position of the first large element of L, or None (peek = +inf)."""
+        return self.pi[self.live[self.s]] if self.s < len(self.live) else None
+
+    def peek(self):
+        p = self.first_large()
+        return math.inf if p is None else self.alpha[p]
+
+    def small_set(self):
+        return {self.pi[r] for r in self.live[:self.s]}
 
     def members(self):
-        """Indices currently in L, in sorted order."""
-        out, node = [], self.next[self.sentinel]
-        while node != self.sentinel:
+        return {self.pi[r] for r in self.live}
+
+    # -- the interface's updates ----------------------------------------------
+    def delete(self, i: int) -> None:
+        r = self.rank[i]
+        at = bisect.bisect_left(self.live, r)
+        assert at < len(self.live) and self.live[at] == r, "delete of an element not in L"
+        del self.live[at]
+        self._removed.append(i)
+        self.s = max(0, self.s - 1)
+
+    def undelete(self, i: int) -> None:
+        assert self._removed and self._removed[-1] == i, "undeletions must be properly nested"
+        self._removed.pop()
+        bisect.insort(self.live, self.rank[i])
+
+    def unwind(self) -> None:
+        for i in reversed(range(len(self.alpha))):
+            self.delete(i)
+
+    def advance(self) -> None:
+        assert self.s < len(self.live), "advance past the end of L"
+        self.s += 1
+
+
+class DancingLinks:
+    """prev / next arrays over nodes 0 .. k-1 plus a sentinel node k, linked
+    in the stable sorted order of the block; equations del and undo-del of
+    Section 4 as the only updates."""
+
+    def __init__(self, alpha):
+        self.k = len(alpha)
+        pi, _ = stable_order(alpha)
+        ring = [self.k] + pi
+        self.next = [0] * (self.k + 1)
+        self.prev = [0] * (self.k + 1)
+        for a, b in zip(ring, ring[1:] + ring[:1]):
+            self.next[a] = b
+            self.prev[b] = a
+
+    def remove(self, i: int) -> None:         # equation del
+        self.next[self.prev[i]] = self.next[i]
+        self.prev[self.next[i]] = self.prev[i]
+
+    def restore(self, i: int) -> None:        # equation undo-del
+        self.next[self.prev[i]] = i
+        self.prev[self.next[i]] = i
+
+    def walk(self):
+        out, node = [], self.next[self.k]
+        while node != self.k:
             out.append(node)
             node = self.next[node]
         return out
 
-    def small_set(self):
-        return self.members()[: self.s]
-
-    # -- updates ----------------------------------------------------------
-    def _unlink(self, i: int) -> None:
-        # equation del: prev[next[i]] <- prev[i], next[prev[i]] <- next[i]
-        before, after = self.prev[i], self.next[i]
-        self.next[before] = after
-        self.prev[after] = before
-
-    def _relink(self, i: int) -> None:
-        # equation undo-del: prev[next[i]] <- i, next[prev[i]] <- i
-        self.next[self.prev[i]] = i
-        self.prev[self.next[i]] = i
-
-    def delete(self, i: int) -> None:
-        """Remove alpha[i] from L; s becomes max(0, s - 1)."""
-        was_small = self.is_small(i)
-        self._unlink(i)
-        if was_small:
-            self.s -= 1
-            return
-        if self.m == i:
-            # i's own pointers still name its old successor
-            self.m = self.next[i]
-        if self.s > 0:
-            self.m = self.prev[self.m]
-            self.s -= 1
-
-    def undelete(self, i: int) -> None:
-        """Put alpha[i] back into L (only as the inverse of the latest delete)."""
-        self._relink(i)
-        if self.is_small(i):
-            self.m = self.prev[self.m]
-
-    def unwind(self) -> None:
-        """delete(k-1), ..., delete(0); afterwards L is empty, m = k, s = 0."""
-        for i in range(self.size - 1, -1, -1):
-            self._unlink(i)
-        self.m = self.sentinel
-        self.s = 0
-
-    def advance(self) -> None:
-        self.m = self.next[self.m]
-        self.s += 1
-
 
 def sort_median(x, k: int, trace=None):
-    """Median filter of x with odd window k by sorting + post-processing.
+    """Median filter of x with odd window k by the steps of Fig. postprocess.
 
-    Returns (y, argmed) as Python lists (argmed = index into x of the median
-    element).  If ``trace`` is a list, one dict per printed output after the
-    first is appended with the block states, for the invariant tests.
+    Returns (y, argmed) as lists (argmed = index into x of the printed
+    element).  If ``trace`` is a list, every printed output after the first
+    appends the sets S_A, S_B, L_A, L_B before step (dagger), after the
+    delete / undelete, and before the print, with s_A and s_B.
     """
     n = len(x)
     if k < 1 or k % 2 == 0 or k > n:
         raise ValueError("need odd 1 <= k <= n")
     h = (k - 1) // 2
-    nblocks = -(-n // k)
-    blocks = [x[j * k:(j + 1) * k] for j in range(nblocks)]
+    blocks = [list(x[j:j + k]) for j in range(0, n, k)]
 
-    B = SortedBlock(blocks[0], h)
-    y = [B.peek()]
-    arg = [B.m]
-    for j in range(1, nblocks):
-        A = B
-        B = SortedBlock(blocks[j], h)
+    def sets(A, B):
+        return dict(SA=A.small_set(), SB=B.small_set(), LA=A.members(), LB=B.members())
+
+    B = RankBlock(blocks[0], h)
+    y, arg = [B.peek()], [B.first_large()]               # step (double dagger)
+    for j in range(1, len(blocks)):
+        A, B = B, RankBlock(blocks[j], h)
         B.unwind()
         for i in range(len(blocks[j])):
-            pre = None
-            if trace is not None:
-                pre = dict(SA=set(A.small_set()), SB=set(B.small_set()),
-                           LA=set(A.members()), LB=set(B.members()))
-            A.delete(i)
+            before = sets(A, B) if trace is not None else None
+            A.delete(i)                                  # step (dagger)
             B.undelete(i)
-            mid = None
-            if trace is not None:
-                mid = dict(SA=set(A.small_set()), SB=set(B.small_set()),
-                           LA=set(A.members()), LB=set(B.members()))
+            middle = sets(A, B) if trace is not None else None
             if A.small() + B.small() < h:
-                if A.peek() <= B.peek():
-                    A.advance()
-                else:
-                    B.advance()
-            if A.peek() <= B.peek():
-                y.append(A.peek())
-                arg.append((j - 1) * k + A.m)
-            else:
-                y.append(B.peek())
-                arg.append(j * k + B.m)
+                (A if A.peek() <= B.peek() else B).advance()
+            take_a = A.peek() <= B.peek()                # step (inverted dagger)
+            y.append(A.peek() if take_a else B.peek())
+            arg.append((j - 1) * k + A.first_large() if take_a else j * k + B.first_large())
             if trace is not None:
-                trace.append(dict(
-                    j=j, i=i, h=h, alphaA=A.alpha, alphaB=B.alpha,
-                    pre=pre, mid=mid,
-                    post=dict(SA=set(A.small_set()), SB=set(B.small_set()),
-                              LA=set(A.members()), LB=set(B.members())),
-                    sA=A.small(), sB=B.small()))
+                trace.append(dict(j=j, i=i, h=h, alphaA=A.alpha, alphaB=B.alpha,
+                                  pre=before, mid=middle, post=sets(A, B),
+                                  sA=A.small(), sB=B.small()))
     return y, arg

@@ -1,7 +1,11 @@
-"""Pins of the paper-method CPU reference (oracle/paper_method.py).
+"""Pins of the set-level model of the paper's method (oracle/paper_method.py).
 
-* Section 5.1: deletions and undeletions must be properly nested; undoing
-  them in reverse order restores the list exactly.
+* Section 4, equations del / undo-del, and Section 5.1: deletions and
+  undeletions must be properly nested; undoing them in reverse order
+  restores the list exactly.  After unwind every node keeps the neighbours it
+  had when it was deleted: the nearest smaller and larger element among the
+  positions before it (the unwind links the GPU path computes directly).
+* Section 5, Fig. block-if: the model's (L, s) after each operation.
 * Section 6.3, equation (inv): before every output s_A + s_B = h and
   S_A u S_B = H_AB (the h smallest elements of the window).
 * Section 6.3, Lemma 1 and its case-analysis table: with S_A non-empty, the
@@ -21,28 +25,77 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle.paper_method import SortedBlock, sort_median
+from oracle.paper_method import DancingLinks, RankBlock, sort_median, stable_order
 from signals import paper_generator
 
 
 def test_properly_nested_delete_undelete_restores_list():
     rng = np.random.default_rng(0)
     alpha = list(rng.integers(0, 50, size=31))
-    blk = SortedBlock(alpha, 15)
-    before = (list(blk.prev), list(blk.next), blk.members())
+    dl = DancingLinks(alpha)
+    before = (list(dl.prev), list(dl.next), dl.walk())
+    assert dl.walk() == sorted(range(31), key=lambda t: (alpha[t], t))
     # the example of Section 5.1: delete 15, delete 3, undelete 3, undelete 15
-    blk._unlink(15)
-    blk._unlink(3)
-    assert 15 not in blk.members() and 3 not in blk.members()
-    blk._relink(3)
-    blk._relink(15)
-    assert (list(blk.prev), list(blk.next), blk.members()) == before
-    # a full unwind followed by undeleting 0..k-1 rebuilds the sorted list
-    blk.unwind()
-    assert blk.members() == []
-    for i in range(len(alpha)):
-        blk._relink(i)
-        assert blk.members() == sorted(range(i + 1), key=lambda t: (alpha[t], t))
+    dl.remove(15)
+    dl.remove(3)
+    assert 15 not in dl.walk() and 3 not in dl.walk()
+    dl.restore(3)
+    dl.restore(15)
+    assert (list(dl.prev), list(dl.next), dl.walk()) == before
+    # an order that is not properly nested can corrupt the list: with three
+    # consecutive elements u < v < w removed in that order, restoring u, w, v
+    # leaves u and v unreachable
+    u, v, w = before[2][10:13]
+    for e in (u, v, w):
+        dl.remove(e)
+    for e in (u, w, v):
+        dl.restore(e)
+    assert dl.walk() != before[2] and u not in dl.walk()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_unwind_leaves_the_links_of_earlier_neighbours(seed):
+    """delete(k-1), ..., delete(0), then undelete(0), ..., undelete(k-1): at
+    undelete(i) node i is relinked between the nearest smaller and the
+    nearest larger of positions 0 .. i-1 (sentinel k where there is none),
+    and the list is then positions 0 .. i in sorted order."""
+    rng = np.random.default_rng(seed)
+    k = int(rng.integers(1, 40))
+    alpha = list(rng.integers(0, 8 if seed % 2 else 1000, size=k))
+    dl = DancingLinks(alpha)
+    for i in reversed(range(k)):
+        dl.remove(i)
+    assert dl.walk() == []
+    _, rank = stable_order(alpha)
+    for i in range(k):
+        lower = [p for p in range(i) if rank[p] < rank[i]]
+        upper = [p for p in range(i) if rank[p] > rank[i]]
+        assert dl.prev[i] == (max(lower, key=rank.__getitem__) if lower else k)
+        assert dl.next[i] == (min(upper, key=rank.__getitem__) if upper else k)
+        dl.restore(i)
+        assert dl.walk() == sorted(range(i + 1), key=lambda t: (alpha[t], t))
+
+
+def test_block_interface_semantics():
+    """Fig. block-if on a small block: construct, delete (s = max(0, s-1)),
+    undelete (s unchanged), advance, peek (first large or +inf), unwind."""
+    alpha = [7, 3, 9, 3, 1]                    # sorted positions: 4, 1, 3, 0, 2
+    b = RankBlock(alpha, 2)
+    assert b.small() == 2 and b.small_set() == {4, 1} and b.peek() == 3 and b.first_large() == 3
+    b.delete(0)                                # a large element: s = 1
+    assert b.small() == 1 and b.small_set() == {4} and b.first_large() == 1
+    b.delete(4)                                # a small element: s = 0
+    assert b.small() == 0 and b.peek() == 3 and b.first_large() == 1
+    b.undelete(4)                              # back in L, s unchanged: 1 is now first
+    assert b.small() == 0 and b.first_large() == 4 and b.peek() == 1
+    b.advance()
+    b.advance()
+    assert b.small_set() == {4, 1} and b.first_large() == 3
+    with pytest.raises(AssertionError):
+        b.undelete(4)                          # not the latest deletion
+    b.undelete(0)
+    b.unwind()
+    assert b.members() == set() and b.small() == 0 and b.peek() == float("inf")
 
 
 def _ordkey(trace_step, side, idx):
