@@ -183,20 +183,28 @@ mf_status mf_filter_backward_rows(mf_handle h, const float* gy, const int32_t* a
 
 /* The median filter of mf_filter for callers that cannot call cudaMalloc.
  * The paper has no counterpart: this entry point exists because some callers
- * may not allocate device memory -- code that runs while a stream is being
- * captured into a CUDA graph (cudaMalloc cannot be captured), programs whose
- * device memory is handed out only by their own pool or arena, and real-time
- * loops that cannot take an allocation's unbounded latency.  It needs no
- * handle and allocates nothing: its scratch is a fixed 32 MiB device array
- * inside the library, present on every GPU that loads libmf.so until the
- * process exits.
+ * may not allocate device memory -- programs whose device memory is handed
+ * out only by their own pool or arena (which must see no allocation made
+ * behind its back), and real-time loops that cannot take an allocation's
+ * unbounded latency.  It needs no handle and allocates nothing: its scratch
+ * is a fixed 32 MiB device array inside the library, present on every GPU
+ * that loads libmf.so until the process exits.
  *  x, n, k, y, argmed  as mf_filter (device pointers of the current device;
  *                      MF_INT32 or MF_FLOAT32 only, else MF_ERR_DTYPE)
  *  cuda_stream         cudaStream_t to run on (NULL = legacy default stream)
- * Limits: the scratch a call needs is about 14 bytes per input sample
- * (8 * kp + 8 bytes per block of k samples plus 6 * kp per block pair, kp = k
- * rounded up to a multiple of 8), so n is limited to roughly 2.3 million;
- * larger requests return MF_ERR_TOO_LARGE and launch nothing.
+ * Limits: k <= 9,344 (larger windows return MF_ERR_UNSUPPORTED).  The call
+ * always runs the shared-memory pipeline: the tier threshold of
+ * mf_set_tier_threshold does not apply, so for 5,001 <= k <= 9,344, where
+ * mf_filter uses the large-k tier by default, the results are the same but
+ * the time and the scratch differ.  The scratch a call needs is the larger
+ * of 12 * kp bytes per block of k samples plus 6 * kp per block pair, and
+ * 8 * kw + 2 * kp per block pair (kp = k rounded up to a multiple of 8,
+ * kw = k + 3 rounded up to a multiple of 8): about 18 bytes per input
+ * sample for k >= 31, so n is limited to about 1.8 million (1,805,843 at
+ * k = 31, 1,850,849 at k = 1001).  Small k costs more per sample because
+ * kp rounds up: 48 bytes at k = 3 (n <= 699,027), 144 at k = 1
+ * (n <= 233,009).  Larger requests return MF_ERR_TOO_LARGE and launch
+ * nothing.
  * The first call on a device, with that device current, looks up the
  * array's device address and sets the kernels' limits; make that first call
  * before any stream capture.  All calls share the one array: calls whose
@@ -204,7 +212,8 @@ mf_status mf_filter_backward_rows(mf_handle h, const float* gy, const int32_t* a
  * race on it and must be serialised by the caller.  The array keeps the
  * previous call's contents; the kernels write every scratch element before
  * reading it, so nothing needs clearing.
- * Errors: as mf_filter, plus MF_ERR_TOO_LARGE and MF_ERR_DEVICE. */
+ * Errors: as mf_filter for the arguments, plus MF_ERR_UNSUPPORTED
+ * (k > 9,344), MF_ERR_TOO_LARGE and MF_ERR_DEVICE. */
 mf_status mf_filter_noalloc(mf_dtype dtype, const void* x, int64_t n, int32_t k,
                             void* y, int32_t* argmed, void* cuda_stream);
 

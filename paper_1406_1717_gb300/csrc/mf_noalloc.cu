@@ -2,11 +2,10 @@
 // allocation, for callers that cannot call cudaMalloc.
 //
 // The regular entry points keep their scratch in a workspace the handle
-// allocates on first use.  Some callers cannot allow that: code that runs
-// while a stream is being captured into a CUDA graph (cudaMalloc is not a
-// capturable operation), applications whose device memory is handed out only
-// by their own pool or arena and must see no foreign allocation, and real-time
-// loops where an allocation's unbounded latency is not acceptable.  For them
+// allocates on first use.  Some callers cannot allow that: applications whose
+// device memory is handed out only by their own pool or arena and must see no
+// foreign allocation, and real-time loops where an allocation's unbounded
+// latency is not acceptable.  For them
 // this file holds the scratch in a fixed, file-scope device array that exists
 // for as long as the library is loaded.  The caller still passes its own
 // input and output buffers.

@@ -153,16 +153,18 @@ def test_lower_bound_reduction_sorts(handle, h_):
 
 @pytest.mark.parametrize("kind", ["walk_f32", "uniform_i32"])
 def test_full_size_k1001_sampled(handle, kind):
-    """n = 2^26, k = 1001, the configuration the bench times: sampled outputs,
-    including both ends of every sampled block pair."""
+    """n = 2^26, k = 1001, the configuration the bench times: the first and the
+    last output of every one of the 67,041 block pairs (where a pair's chain
+    starts and ends), 10^6 random windows, and both ends of the signal."""
     n, k = 1 << 26, 1001
     x = random_walk_f32(n) if kind == "walk_f32" else uniform_i32(n)
     y, a = gpu_filter(handle, x, k)
     rng = np.random.default_rng(123)
     m = n - k + 1
-    pairs = rng.integers(1, (n + k - 1) // k, size=1500)
-    starts = np.concatenate([(pairs - 1) * k + 1, np.minimum((pairs - 1) * k + k, m - 1),
-                             rng.integers(0, m, size=3000), [0, m - 1]])
+    pairs = np.arange(1, (n + k - 1) // k)                 # every pair j = 1 .. b-1
+    assert pairs.size == 67_041
+    starts = np.unique(np.concatenate([(pairs - 1) * k + 1, np.minimum((pairs - 1) * k + k, m - 1),
+                                       rng.integers(0, m, size=1_000_000), [0, m - 1]]))
     ry, ra = oracle.window_medians(x, k, starts)
     assert_bits_equal(y[starts], ry, f"{kind} sampled")
     np.testing.assert_array_equal(a[starts], ra)

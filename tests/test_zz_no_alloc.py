@@ -1,13 +1,16 @@
 """mf_filter_noalloc: the median filter for callers that cannot allocate
-device memory (for example code that runs during CUDA graph capture, or
-programs whose device memory comes only from their own pool).
+device memory (for example programs whose device memory comes only from their
+own pool, or real-time loops that cannot wait for an allocation).
 
 It runs the same kernels as mf_filter but keeps their scratch in a fixed
 array inside the library instead of a workspace it allocates.  This test
-calls it through the C ABI twice in a row, on different inputs and window
-sizes, and checks each result bit for bit against mf_filter; it also checks
-that a request larger than the fixed array is refused.  The file sorts last
-so that a run stopping at the first failure has already run every other test.
+calls it through the C ABI several times in a row, on different inputs and
+window sizes, and checks each result bit for bit against mf_filter: the fused
+path (k = 1001, k = 31) and, right after them on the scratch they left, the
+four-kernel path (k = 2047).  It also checks the size limit: the largest
+accepted n at k = 1001 runs and matches, one sample more is refused.  The
+file sorts last so that a run stopping at the first failure has already run
+every other test.
 """
 import ctypes
 
@@ -39,7 +42,8 @@ def test_noalloc_matches_mf_filter_on_two_calls_in_a_row():
     lib = mf.load_library()
     stream = torch.cuda.current_stream(DEV)
     cases = [(random_walk_f32(700_001, seed=41), 1001, 1),
-             (uniform_i32(300_007, seed=42), 31, 0)]
+             (uniform_i32(300_007, seed=42), 31, 0),
+             (random_walk_f32(600_011, seed=43), 2047, 1)]
     outs = []
     for x_np, k, code in cases:
         x = torch.from_numpy(x_np).to(DEV)
@@ -67,3 +71,26 @@ def test_noalloc_refuses_requests_beyond_its_scratch():
                                ctypes.c_void_p(y.data_ptr()), None, None)
     assert st == 12                       # MF_ERR_TOO_LARGE, nothing launched
     assert "TOO_LARGE" in mf.mf_status_str(st)
+
+
+def test_noalloc_size_limit_at_k1001():
+    """At k = 1001 the 32 MiB array holds the scratch of n = 1,850,849 samples
+    (the larger of 12 kp bytes per block + 6 kp per pair and 8 kw + 2 kp per
+    pair, kp = 1008, kw = 1008): that n runs and matches mf_filter, one sample
+    more (a new block) is refused."""
+    lib = mf.load_library()
+    k, n_max = 1001, 1_850_849
+    stream = torch.cuda.current_stream(DEV)
+    x_np = uniform_i32(n_max + 1, seed=44)
+    x = torch.from_numpy(x_np).to(DEV)
+    y = torch.full((n_max + 1 - k + 1,), -1, dtype=x.dtype, device=DEV)
+    st = lib.mf_filter_noalloc(0, ctypes.c_void_p(x.data_ptr()), n_max + 1, k,
+                               ctypes.c_void_p(y.data_ptr()), None, ctypes.c_void_p(stream.cuda_stream))
+    assert st == 12
+    st = lib.mf_filter_noalloc(0, ctypes.c_void_p(x.data_ptr()), n_max, k,
+                               ctypes.c_void_p(y.data_ptr()), None, ctypes.c_void_p(stream.cuda_stream))
+    assert st == 0, mf.mf_status_str(st)
+    torch.cuda.synchronize(DEV)
+    ry, _ = _reference(x[:n_max], k)
+    got = y[:n_max - k + 1].cpu().numpy()
+    np.testing.assert_array_equal(got.view(np.uint32), ry.view(np.uint32))
