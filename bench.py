@@ -496,34 +496,46 @@ def bench_small(mf, h, dev, stream, args):
 
 def bench_batched(mf, h, dev, stream, seed, args):
     """4096 signals of log-uniform n and k in one batched call (captured in a
-    CUDA graph and replayed) against a loop of per-signal calls."""
+    CUDA graph and replayed) against a loop of per-signal calls.  The graph is
+    timed with the built-in launch plans and again after the autotuner has
+    chosen each class's sort variant and pairs per CTA on this batch."""
     import torch
+    from paper_1406_1717_gb300 import tune
     from signals import batched_signals
     b = batched_signals(nseg=4096, seed=seed)
     x = torch.from_numpy(b.x).to(dev)
     y = torch.empty(b.y_total, dtype=torch.float32, device=dev)
     segs = mf.make_segments(b.n, b.k, b.x_off, b.y_off)
-    with torch.cuda.stream(stream):
-        mf.mf_filter_batched(h, x, y, segs)
-    stream.synchronize()
-    l0 = mf.mf_launch_count(h)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=stream):
-        mf.mf_set_stream(h, torch.cuda.current_stream(dev))
-        mf.mf_filter_batched(h, x, y, segs)
-    launches_per_call = mf.mf_launch_count(h) - l0
-    mf.mf_set_stream(h, stream)
     reps = max(3, min(args.steps, 10))
+
+    def graph_time():
+        with torch.cuda.stream(stream):
+            mf.mf_filter_batched(h, x, y, segs)
+        stream.synchronize()
+        l0 = mf.mf_launch_count(h)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            mf.mf_set_stream(h, torch.cuda.current_stream(dev))
+            mf.mf_filter_batched(h, x, y, segs)
+        launches = mf.mf_launch_count(h) - l0
+        mf.mf_set_stream(h, stream)
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                g.replay()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                g.replay()
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / reps, launches
+
+    builtin_ms, _ = graph_time()
     with torch.cuda.stream(stream):
-        for _ in range(2):
-            g.replay()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            g.replay()
-        e1.record(stream)
+        tuned = tune.tune_batched(h, x, segs)
     stream.synchronize()
-    graph_ms = e0.elapsed_time(e1) / reps
+    graph_ms, launches_per_call = graph_time()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         e0.record(stream)
         for _ in range(reps):
@@ -543,6 +555,10 @@ def bench_batched(mf, h, dev, stream, seed, args):
     return {"workload": "4096 float32 signals, n log-uniform [1e3, 262144], odd k log-uniform "
                         "[3, 4095], 10% +-1e3 impulses",
             "outputs": int(b.y_total), "graph_ms": graph_ms, "batched_ms": batched_ms,
+            "graph_ms_builtin_plans": builtin_ms,
+            "tuned": {c: {kk: v[kk] for kk in ("signals", "sort_variant", "sort_pairs_per_cta",
+                                                "store_pairs_per_cta")}
+                      for c, v in tuned.items()},
             "per_signal_loop_ms": loop_ms, "launches_per_batched_call": int(launches_per_call),
             "value_graph": b.y_total / (graph_ms * 1e-3) / 1e9,
             "value_per_signal": b.y_total / (loop_ms * 1e-3) / 1e9, "unit": UNIT,

@@ -231,6 +231,24 @@ mf_status mf_launch_count(mf_handle h, uint64_t* count);
 mf_status mf_set_tuning(mf_handle h, int32_t k, int32_t sort_pairs_per_cta,
                         int32_t store_pairs_per_cta);
 
+/* Block-sort variant for the window-size class that contains k (the classes
+ * of mf_set_tuning).  Section 3 leaves the piecewise sort open ("any sorting
+ * algorithm"); both variants give the same stable order, so the results do
+ * not change, only the time:
+ *  0  built-in choice;
+ *  1  merge-sort tiles: a warp sorts 1024-element tiles (odd-even network per
+ *     lane, merge-path rounds) in the same kernel that builds both lists
+ *     (4-byte elements with k <= 1021; elsewhere variant 2 is used);
+ *  2  warp LSD radix sort (8-bit digits) in a kernel of its own, followed by
+ *     separate unwind, chain and store kernels;
+ *  3  as 1, but every tile is first tested for blocks that are already in
+ *     order (ascending, or strictly descending) and those tiles are not
+ *     sorted (Section 1: an adaptive sort gives an adaptive median filter);
+ *     the test costs a few percent on unordered input.
+ * Used by the autotuner.  Errors: MF_ERR_NULL, MF_ERR_K_GT_N (k < 1),
+ * MF_ERR_UNSUPPORTED (variant outside 0 .. 3). */
+mf_status mf_set_sort_variant(mf_handle h, int32_t k, int32_t variant);
+
 /* Device workspace (bytes) that mf_filter_batched with these descriptors
  * needs on this handle (host-only computation; the request server admits
  * work by it).  Errors: MF_ERR_NULL, MF_ERR_BAD_SEGMENT. */

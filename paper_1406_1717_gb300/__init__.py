@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH):
             "mf_launch_count": ([vp, c.POINTER(c.c_uint64)], c.c_int),
             "mf_set_timing": ([vp, c.c_int], c.c_int),
             "mf_set_tuning": ([vp, i32, i32, i32], c.c_int),
+            "mf_set_sort_variant": ([vp, i32, i32], c.c_int),
             "mf_set_tier_threshold": ([vp, i32], c.c_int),
             "mf_get_tier_threshold": ([vp, c.POINTER(i32)], c.c_int),
             "mf_batched_workspace_bytes": ([vp, c.c_int, vp, i32, c.POINTER(sz)], c.c_int),
@@ -237,6 +238,13 @@ def mf_set_tuning(handle, k: int, sort_pairs_per_cta: int = 0, store_pairs_per_c
     """Launch-plan choice for the window-size class containing k (0 = built-in)."""
     _check(load_library().mf_set_tuning(handle, int(k), int(sort_pairs_per_cta),
                                         int(store_pairs_per_cta)), "mf_set_tuning")
+
+
+def mf_set_sort_variant(handle, k: int, variant: int = 0):
+    """Block-sort variant for the class containing k: 0 built-in, 1 merge-sort
+    tiles (fused path), 2 warp radix sort (four-kernel path), 3 merge-sort
+    tiles that skip tiles of ordered blocks."""
+    _check(load_library().mf_set_sort_variant(handle, int(k), int(variant)), "mf_set_sort_variant")
 
 
 def mf_set_tier_threshold(handle, k_large_from: int = 0):

@@ -118,14 +118,14 @@ size_t signal_workspace_bytes(mf_handle h, int64_t n, int k, bool wide) {
 }
 
 // Workspace of a batched call: the pipeline group and, reusing the same
-// memory afterwards, the largest large-k signal.
+// memory afterwards, the large-k group (all its signals at once).
 size_t batched_need(mf_handle h, const mf_segment* segs, int32_t nseg, bool wide) {
-    std::vector<int64_t> nn;
-    std::vector<int32_t> kk;
-    size_t big_need = 0;
+    std::vector<int64_t> nn, bn;
+    std::vector<int32_t> kk, bk;
     for (int32_t s = 0; s < nseg; ++s) {
         if (use_large(h, segs[s].k, wide)) {
-            big_need = std::max(big_need, mf::large_workspace_bytes(segs[s].n, segs[s].k, wide));
+            bn.push_back(segs[s].n);
+            bk.push_back(segs[s].k);
         } else {
             nn.push_back(segs[s].n);
             kk.push_back(segs[s].k);
@@ -133,6 +133,8 @@ size_t batched_need(mf_handle h, const mf_segment* segs, int32_t nseg, bool wide
     }
     const size_t small_need =
         kk.empty() ? 0 : mf::pipeline_batched_workspace_bytes(nn.data(), kk.data(), (int)kk.size());
+    const size_t big_need =
+        bk.empty() ? 0 : mf::large_batched_workspace_bytes(bn.data(), bk.data(), (int)bk.size(), wide);
     return std::max(small_need, big_need);
 }
 
@@ -200,7 +202,7 @@ mf_status mf_create(mf_handle* out, int device, void* cuda_stream, size_t max_wo
     h->max_k = mf::kLargeMaxK;
     h->large_from_k = std::min(mf::kLargeFromK, mf::pipeline_max_k() + 1);
     h->events_made = false;
-    for (int c = 0; c < mf::kNumTuneClasses; ++c) h->tune[c] = mf::Tuning{0, 0};
+    for (int c = 0; c < mf::kNumTuneClasses; ++c) h->tune[c] = mf::Tuning{0, 0, 0};
     h->stats.tune = h->tune;
     h->stage = nullptr;
     h->stage_size = 0;
@@ -369,33 +371,28 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
     DeviceGuard g(h->device);
     if (!g.ok) return MF_ERR_CUDA;
     if (nseg == 0) return MF_OK;
-    // signals of the shared-memory pipeline go into one batched launch group;
-    // the large-k ones follow one by one, reusing the same workspace
-    std::vector<int64_t> xo, nn, yo;
-    std::vector<int32_t> kk, big;
+    // signals of the shared-memory pipeline go into one batched launch group
+    // (one launch per kernel and window class), then the large-k ones into one
+    // launch sequence of the global-memory tier, reusing the same workspace;
+    // the number of launches depends on neither the number of signals nor the
+    // number of large-k signals
+    std::vector<int64_t> xo, nn, yo, bxo, bnn, byo;
+    std::vector<int32_t> kk, bkk;
     for (int32_t s = 0; s < nseg; ++s) {
-        if (use_large(h, segs[s].k, el.wide)) {
-            big.push_back(s);
-            continue;
+        const mf_segment& d = segs[s];
+        if (use_large(h, d.k, el.wide)) {
+            bxo.push_back(d.x_off); bnn.push_back(d.n); byo.push_back(d.y_off); bkk.push_back(d.k);
+        } else {
+            xo.push_back(d.x_off); nn.push_back(d.n); yo.push_back(d.y_off); kk.push_back(d.k);
         }
-        xo.push_back(segs[s].x_off); nn.push_back(segs[s].n);
-        yo.push_back(segs[s].y_off); kk.push_back(segs[s].k);
     }
-    const int32_t nsmall = (int32_t)kk.size();
+    const int32_t nsmall = (int32_t)kk.size(), nbig = (int32_t)bkk.size();
     const size_t need = batched_need(h, segs, nseg, el.wide);
     mf_status st = ensure_workspace(h, need);
     if (st != MF_OK) return st;
-    if (nsmall == 0) {
-        for (int32_t s : big) {
-            const mf_segment& d = segs[s];
-            cudaError_t e = mf::launch_large((const char*)x + d.x_off * eb, d.n, d.k, (d.k - 1) / 2, el,
-                                             (char*)y + d.y_off * eb, argmed ? argmed + d.y_off : nullptr,
-                                             h->ws, need, h->stream, &h->stats);
-            if (e != cudaSuccess) return MF_ERR_CUDA;
-        }
-        return MF_OK;
-    }
-    const size_t stage_need = (size_t)nsmall * sizeof(mf::PipeParams);
+    // pinned staging: the pipeline's descriptors, then the large tier's
+    const size_t small_stage = ((size_t)nsmall * sizeof(mf::PipeParams) + 255) & ~size_t(255);
+    const size_t stage_need = small_stage + (size_t)nbig * mf::large_descriptor_bytes();
     const bool cap = capturing(h->stream);
     if (!cap) {
         if (h->stage_in_graph) {                      // leave that buffer to its graph
@@ -416,18 +413,16 @@ mf_status mf_filter_batched(mf_handle h, mf_dtype dtype, const void* x, void* y,
     } else if (h->stage_size < stage_need || h->stage_in_graph) {
         return MF_ERR_OOM;                            // make one uncaptured call of this size first
     }
-    cudaError_t e = mf::launch_pipeline_batched(x, y, argmed,
-                                                el, xo.data(), nn.data(), yo.data(),
-                                                kk.data(), nsmall, h->ws, need, h->stage, h->stage_size,
-                                                h->num_sms, h->stream, &h->stats);
+    cudaError_t e = cudaSuccess;
+    if (nsmall > 0)
+        e = mf::launch_pipeline_batched(x, y, argmed, el, xo.data(), nn.data(), yo.data(),
+                                        kk.data(), nsmall, h->ws, need, h->stage, small_stage,
+                                        h->num_sms, h->stream, &h->stats);
+    if (e == cudaSuccess && nbig > 0)
+        e = mf::launch_large_batched(x, y, argmed, el, bxo.data(), bnn.data(), byo.data(), bkk.data(),
+                                     nbig, h->ws, need, (char*)h->stage + small_stage,
+                                     stage_need - small_stage, h->stream, &h->stats);
     if (e != cudaSuccess) return MF_ERR_CUDA;
-    for (int32_t s : big) {
-        const mf_segment& d = segs[s];
-        e = mf::launch_large((const char*)x + d.x_off * eb, d.n, d.k, (d.k - 1) / 2, el,
-                             (char*)y + d.y_off * eb, argmed ? argmed + d.y_off : nullptr,
-                             h->ws, need, h->stream, &h->stats);
-        if (e != cudaSuccess) return MF_ERR_CUDA;
-    }
     if (cap) h->stage_in_graph = true;
     else cudaEventRecord(h->stage_done, h->stream);
     return MF_OK;
@@ -474,6 +469,14 @@ mf_status mf_set_tuning(mf_handle h, int32_t k, int32_t sort_pairs_per_cta, int3
     mf::Tuning& t = h->tune[mf::tune_class_of(k)];
     t.sort_G = sort_pairs_per_cta > 0 ? sort_pairs_per_cta : 0;
     t.epi_G = store_pairs_per_cta > 0 ? store_pairs_per_cta : 0;
+    return MF_OK;
+}
+
+mf_status mf_set_sort_variant(mf_handle h, int32_t k, int32_t variant) {
+    if (!h) return MF_ERR_NULL;
+    if (k < 1) return MF_ERR_K_GT_N;
+    if (variant < 0 || variant > 3) return MF_ERR_UNSUPPORTED;
+    h->tune[mf::tune_class_of(k)].variant = variant;
     return MF_OK;
 }
 

@@ -48,6 +48,10 @@ struct SegTable {
 struct Tuning {
     int sort_G;               // pairs per sortmerge CTA
     int epi_G;                // pairs per epilogue CTA
+    int variant;              // block sort: 0 built-in, 1 merge-sort tiles (fused path,
+                              // 4-byte elements, k <= kFusedMaxK), 2 warp radix sort
+                              // (four-kernel path), 3 merge-sort tiles that skip
+                              // tiles of ordered blocks
 };
 struct SortPlan {
     uint32_t off_keyA, off_keyB, off_valA, off_valB, off_hist;
@@ -101,7 +105,8 @@ struct Elem {
 int pipeline_max_k(bool wide = false);
 size_t sortlist_smem_bytes(int warps);
 cudaError_t sortlist_setup();
-cudaError_t launch_sortlist(const SegTable& tab, int64_t items, int warps, cudaStream_t stream);
+cudaError_t launch_sortlist(const SegTable& tab, int64_t items, int warps, bool adaptive,
+                            cudaStream_t stream);
 size_t pipeline_workspace_bytes(int64_t n, int k);
 cudaError_t pipeline_setup();
 // rank: 0-based order statistic printed for every window (the median of an
@@ -131,6 +136,17 @@ size_t large_workspace_bytes(int64_t n, int k, bool wide);
 cudaError_t launch_large(const void* x, int64_t n, int k, int rank, Elem el, void* y,
                          int32_t* argmed, void* ws, size_t ws_bytes, cudaStream_t stream,
                          LaunchStats* stats);
+// Every large-k signal of a batch in one launch sequence (median rank of each
+// signal): descriptors staged in `stage` (host memory of at least
+// nseg * large_descriptor_bytes(), unchanged until the copy ran), workspace
+// large_batched_workspace_bytes().
+size_t large_descriptor_bytes();
+size_t large_batched_workspace_bytes(const int64_t* n, const int32_t* k, int nseg, bool wide);
+cudaError_t launch_large_batched(const void* x, void* y, int32_t* argmed, Elem el,
+                                 const int64_t* x_off, const int64_t* n, const int64_t* y_off,
+                                 const int32_t* k, int nseg, void* ws, size_t ws_bytes,
+                                 void* stage, size_t stage_bytes, cudaStream_t stream,
+                                 LaunchStats* stats);
 
 cudaError_t backward_setup();
 cudaError_t launch_backward(const float* gy, const int32_t* argmed, int64_t rows, int64_t n, int k,

@@ -43,7 +43,8 @@
 namespace mf {
 
 constexpr int kChunk = 1024;                     // elements per warp sort
-constexpr int kUnwindRun = 1024;                 // positions per unwind CTA
+constexpr int kUnwindRun = 1024;                 // positions per unwind run
+constexpr int kUnwindRunsPerCta = 8;             // consecutive runs of one unwind CTA
 constexpr uint32_t kBFlag = 0x80000000u;          // node id of B's element
 
 struct LargeParams {
@@ -67,7 +68,46 @@ struct LargeParams {
     uint32_t* out;                               // [npairs][kp] printed node at step i
     int4* seg;                                   // [npairs][S] (mA, mB, sA, sB) before step i0
     uint2* lists;                                // [npairs][S][LN] (next, prev) per rank node
+    int cpb;                                     // 1024-element chunks per block
+    int ntier;                                   // merge tiers (runs of 1024 -> one run per block)
+    const void* ksort;                           // keyA or keyB: the sorted keys after the tiers
+    const uint32_t* vsort;                       // valA or valB: the sorted positions
+    int64_t start[15];                           // this signal's first item in each launch
 };
+
+// Launches of the tier and their work items.  One launch serves every signal
+// of a call (one signal, or the large-k signals of a batch): an item finds its
+// signal by binary search over the signals' first items.
+enum {
+    kLChunk = 0,          // warp: (block, chunk)
+    kLMerge0 = 1,         // thread: 4 outputs of merge tier t (kLMerge0 + t)
+    kLRanks = 9,          // thread: (block, sorted index)
+    kLJrank = 10,         // thread: (pair, element of A or B)
+    kLUnwind = 11,        // CTA: (block >= 1, run of kUnwindRun positions)
+    kLSeg = 12,           // CTA: (pair, segment)
+    kLChain = 13,         // thread: (pair, segment)
+    kLEpi = 14            // thread: output
+};
+constexpr int kLMaxTiers = 8;                    // 1024 << 8 > kLargeMaxK
+
+struct LargeTable {
+    const LargeParams* segs;                     // device table (nullptr: `one`)
+    int nseg;
+    LargeParams one;
+};
+
+__device__ __forceinline__ LargeParams find_large(const LargeTable& t, int kind, int64_t item,
+                                                  int64_t* local)
+{
+    if (t.segs == nullptr) { *local = item; return t.one; }
+    int lo = 0, hi = t.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.segs[mid].start[kind] <= item) lo = mid; else hi = mid - 1;
+    }
+    *local = item - t.segs[lo].start[kind];      // indexed in global memory, not in the copy
+    return t.segs[lo];
+}
 
 __device__ __forceinline__ int block_len(const LargeParams& p, int64_t b) {
     const int64_t r = p.n - b * (int64_t)p.k;
@@ -128,14 +168,16 @@ __host__ __device__ constexpr size_t chunk_warp_bytes() { return (size_t)kChunk 
 
 template <typename KeyT>
 __global__ void __launch_bounds__(256)
-large_chunk_sort(LargeParams p, int chunks_per_block)
+large_chunk_sort(LargeTable tab, int64_t items)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t id = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (id >= p.nblocks * chunks_per_block) return;
-    const int64_t b = id / chunks_per_block;
-    const int c = (int)(id - b * chunks_per_block);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (gw >= items) return;
+    int64_t id;
+    const LargeParams p = find_large(tab, kLChunk, gw, &id);
+    const int64_t b = id / p.cpb;
+    const int c = (int)(id - b * p.cpb);
     const int NB = block_len(p, b);
     const int lo = c * kChunk;
     const int cnt = min(kChunk, NB - lo);
@@ -159,12 +201,21 @@ large_chunk_sort(LargeParams p, int chunks_per_block)
 // thread writes 4 consecutive outputs after a merge-path search
 template <typename KeyT>
 __global__ void __launch_bounds__(256)
-large_merge(LargeParams p, const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
-            KeyT* __restrict__ kout, uint32_t* __restrict__ vout, int R, int per_block)
+large_merge(LargeTable tab, int tier, int64_t items)
 {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= items) return;
+    int64_t gid;
+    const LargeParams p = find_large(tab, kLMerge0 + tier, g, &gid);
+    // tier t reads the buffers tier t-1 wrote (A for even t, B for odd t)
+    const bool odd = (tier & 1) != 0;
+    const KeyT* __restrict__ kin = reinterpret_cast<const KeyT*>(odd ? p.keyB : p.keyA);
+    KeyT* __restrict__ kout = reinterpret_cast<KeyT*>(odd ? p.keyA : p.keyB);
+    const uint32_t* __restrict__ vin = odd ? p.valB : p.valA;
+    uint32_t* __restrict__ vout = odd ? p.valA : p.valB;
+    const int R = kChunk << tier;
+    const int per_block = (int)(p.kp / 4);
     const int64_t b = gid / per_block;
-    if (b >= p.nblocks) return;
     const int o = (int)(gid - b * per_block) * 4;
     const int NB = block_len(p, b);
     if (o >= NB) return;
@@ -189,11 +240,14 @@ large_merge(LargeParams p, const KeyT* __restrict__ kin, const uint32_t* __restr
 }
 
 __global__ void __launch_bounds__(256)
-large_ranks(LargeParams p, const uint32_t* __restrict__ vs)
+large_ranks(LargeTable tab, int64_t items)
 {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= items) return;
+    int64_t gid;
+    const LargeParams p = find_large(tab, kLRanks, g, &gid);
+    const uint32_t* __restrict__ vs = p.vsort;
     const int64_t b = gid / p.kp;
-    if (b >= p.nblocks) return;
     const int t = (int)(gid - b * p.kp);
     if (t >= block_len(p, b)) return;
     p.rnk[b * p.kp + vs[b * p.kp + t]] = (uint32_t)t;
@@ -203,12 +257,16 @@ large_ranks(LargeParams p, const uint32_t* __restrict__ vs)
 // A's t-th smallest -> t + #{B keys < key}; B's u-th -> u + #{A keys <= key}
 template <typename KeyT>
 __global__ void __launch_bounds__(256)
-large_jrank(LargeParams p, const KeyT* __restrict__ ks, const uint32_t* __restrict__ vs)
+large_jrank(LargeTable tab, int64_t items)
 {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= items) return;
+    int64_t gid;
+    const LargeParams p = find_large(tab, kLJrank, g, &gid);
+    const KeyT* __restrict__ ks = reinterpret_cast<const KeyT*>(p.ksort);
+    const uint32_t* __restrict__ vs = p.vsort;
     const int64_t per_pair = 2 * p.kp;
     const int64_t q = gid / per_pair;
-    if (q >= p.npairs) return;
     const int e = (int)(gid - q * per_pair);
     const int NA = p.k, NB = block_len(p, q + 1);
     const int64_t abase = q * p.kp, bbase = (q + 1) * p.kp;
@@ -232,58 +290,175 @@ large_jrank(LargeParams p, const KeyT* __restrict__ ks, const uint32_t* __restri
     }
 }
 
-// Unwind links of block b >= 1 (blockIdx.x = b - 1), positions
-// [i0, i0 + kUnwindRun) (blockIdx.y = run).  The bitset of the ranks of all
-// positions < i0 is built from the sorted order; then one thread inserts the
-// run's ranks in position order, recording for each its nearest set ranks
-// below and above; the CTA turns those ranks into nodes.
+// Unwind links of block b >= 1 (Section 4, "Unwind": the links of position
+// p are the nearest smaller and larger ranks among the positions before p).
+// One CTA takes kUnwindRunsPerCta consecutive runs of kUnwindRun positions
+// (item = (b - 1) * groups + group).  It keeps the bitset W of the ranks of
+// all positions before the current run (built once from the sorted order,
+// then grown run by run) and, for each run, takes the better of two
+// candidates per position:
+//  * among the positions before the run: a query of W (all threads);
+//  * among the earlier positions of the run: the run's ranks are numbered
+//    0 .. len-1 in sorted order ("local ranks", prefix popcounts of the bitset
+//    R of the run's ranks), and warp 0 walks the run as 32 lanes of 32
+//    positions, each lane's 1024-bit local bitset seeded with the local ranks
+//    of the lanes before it (an exclusive OR-scan over lanes), as the fused
+//    sort kernel does for a whole block.
+// The ranks are then turned into nodes.
 __global__ void __launch_bounds__(256)
-large_unwind(LargeParams p, const uint32_t* __restrict__ vs, int nw, int ns)
+large_unwind(LargeTable tab)
 {
     extern __shared__ __align__(16) uint32_t sw[];
-    const int64_t b = 1 + (int64_t)blockIdx.x;
+    int64_t id;
+    const LargeParams p = find_large(tab, kLUnwind, blockIdx.x, &id);
+    const uint32_t* __restrict__ vs = p.vsort;
+    const int runs = (p.k + kUnwindRun - 1) / kUnwindRun;
+    const int groups = (runs + kUnwindRunsPerCta - 1) / kUnwindRunsPerCta;
+    const int nw = (p.k + 31) / 32, ns = (nw + 31) / 32;
+    const int64_t b = 1 + id / groups;
     const int NB = block_len(p, b);
-    const int i0 = blockIdx.y * kUnwindRun;
-    if (i0 >= NB) return;
-    const int len = min(kUnwindRun, NB - i0);
+    const int run0 = (int)(id - (b - 1) * groups) * kUnwindRunsPerCta;
+    const int run1 = min(run0 + kUnwindRunsPerCta, (NB + kUnwindRun - 1) / kUnwindRun);
+    if (run0 >= run1) return;
     int2* pp = reinterpret_cast<int2*>(sw);       // kUnwindRun (pred, succ) ranks
     uint32_t* rr = sw + 2 * kUnwindRun;            // kUnwindRun ranks of the run
-    uint32_t* W = rr + kUnwindRun;                 // nw words
-    uint32_t* W1 = W + nw;                         // ns words
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    uint32_t* srt = rr + kUnwindRun;               // kUnwindRun: rank of local rank j
+    uint32_t* lrk = srt + kUnwindRun;              // kUnwindRun: local rank of position t
+    uint32_t* lb = lrk + kUnwindRun;               // 32 x 32 local bitsets (word w of lane L at 32 w + L)
+    uint32_t* cs = lb + 32 * 32;                   // 256 per-thread counts (scan)
+    uint32_t* W = cs + 256;                        // nw words: ranks of positions before the run
+    uint32_t* W1 = W + nw;                         // ns words: summary of W
+    uint32_t* R = W1 + ns;                         // nw words: ranks of the run
+    uint32_t* Rc = R + nw;                         // nw words: popcount of R before word w
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     const int64_t base = b * p.kp;
-    for (int w = warp; w < nw; w += nwarp) {
-        const int r = (w << 5) + lane;
-        const bool set = r < NB && (int)__ldg(vs + base + r) < i0;
-        const uint32_t word = __ballot_sync(kFull, set);
-        if (lane == 0) W[w] = word;
-    }
-    for (int t = threadIdx.x; t < len; t += blockDim.x) rr[t] = __ldg(p.rnk + base + i0 + t);
-    __syncthreads();
-    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
-        uint32_t sm = 0;
-        for (int c = 0; c < 32 && (s << 5) + c < nw; ++c)
-            if (W[(s << 5) + c]) sm |= 1u << c;
-        W1[s] = sm;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int t = 0; t < len; ++t) {
-            const int r = (int)rr[t];
-            pp[t] = make_int2(bits_last_before(W, W1, nw, r), bits_first_from(W, W1, nw, ns, r + 1));
-            W[r >> 5] |= 1u << (r & 31);
-            W1[r >> 10] |= 1u << ((r >> 5) & 31);
-        }
-    }
-    __syncthreads();
-    // block ranks -> rank nodes of pair b-1 (B's t-th smallest is node jrs[t])
     const uint32_t sentB = 2u * (uint32_t)p.k + 1u;
     const uint32_t* jrs = p.jrs + (b - 1) * p.kp;
-    for (int t = threadIdx.x; t < len; t += blockDim.x) {
-        const int2 q = pp[t];
-        const uint32_t pv = q.x >= 0 ? __ldg(jrs + q.x) : sentB;
-        const uint32_t nx = q.y >= 0 ? __ldg(jrs + q.y) : sentB;
-        p.ulink[base + i0 + t] = make_uint2(pv, nx);
+    {
+        const int first = run0 * kUnwindRun;
+        for (int w = warp; w < nw; w += nwarp) {
+            const int r = (w << 5) + lane;
+            const bool set = r < NB && (int)__ldg(vs + base + r) < first;
+            const uint32_t word = __ballot_sync(kFull, set);
+            if (lane == 0) W[w] = word;
+        }
+        __syncthreads();
+        for (int sI = tid; sI < ns; sI += blockDim.x) {
+            uint32_t sm = 0;
+            for (int c = 0; c < 32 && (sI << 5) + c < nw; ++c)
+                if (W[(sI << 5) + c]) sm |= 1u << c;
+            W1[sI] = sm;
+        }
+    }
+    const int per = (nw + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int w0 = min(nw, tid * per), w1 = min(nw, w0 + per);
+    for (int run = run0; run < run1; ++run) {
+        const int i0 = run * kUnwindRun;
+        const int len = min(kUnwindRun, NB - i0);
+        for (int w = w0; w < w1; ++w) R[w] = 0u;
+        for (int t = tid; t < len; t += blockDim.x) rr[t] = __ldg(p.rnk + base + i0 + t);
+        __syncthreads();
+        for (int t = tid; t < len; t += blockDim.x) atomicOr(&R[rr[t] >> 5], 1u << (rr[t] & 31));
+        __syncthreads();
+        // exclusive prefix popcount of R: thread t sums words [w0, w1)
+        uint32_t cnt = 0;
+        for (int w = w0; w < w1; ++w) cnt += __popc(R[w]);
+        cs[tid] = cnt;
+        __syncthreads();
+        if (warp == 0) {                           // scan of the 256 counts, 8 per lane
+            uint32_t c8[8], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) { c8[q] = cs[8 * lane + q]; sum += c8[q]; }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t v = __shfl_up_sync(kFull, incl, off);
+                if (lane >= off) incl += v;
+            }
+            uint32_t acc = incl - sum;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) { cs[8 * lane + q] = acc; acc += c8[q]; }
+        }
+        __syncthreads();
+        cnt = cs[tid];
+        for (int w = w0; w < w1; ++w) { Rc[w] = cnt; cnt += __popc(R[w]); }
+        __syncthreads();
+        // local ranks, sorted run; candidates among the positions before the run
+        for (int t = tid; t < len; t += blockDim.x) {
+            const uint32_t r = rr[t];
+            const uint32_t lr = Rc[r >> 5] + __popc(R[r >> 5] & ((1u << (r & 31)) - 1u));
+            lrk[t] = lr;
+            srt[lr] = r;
+            int2 q = make_int2(-1, -1);
+            if (i0 > 0)
+                q = make_int2(bits_last_before(W, W1, nw, (int)r), bits_first_from(W, W1, nw, ns, (int)r + 1));
+            pp[t] = q;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // lane L: positions [32 L, 32 L + 32) of the run; bitsets over local ranks
+            const int q0 = min(32 * lane, len), q1 = min(q0 + 32, len);
+            uint32_t* bw = lb + lane;
+            for (int w = 0; w < 32; ++w) bw[32 * w] = 0u;
+            for (int t = q0; t < q1; ++t) bw[32 * (lrk[t] >> 5)] |= 1u << (lrk[t] & 31);
+            __syncwarp();
+            {
+                // exclusive OR-scan over lanes, transposed: lane w scans word w
+                // of all 32 lanes' bitsets (rotated order, bank (i + w) % 32)
+                uint32_t* col = lb + 32 * lane;
+                uint32_t c[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) c[i] = col[(i + lane) & 31];
+                uint32_t low = 0u;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) low |= (i >= 32 - lane) ? c[i] : 0u;
+                uint32_t acc_hi = 0u, acc_lo = 0u;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const bool hi_part = i < 32 - lane;
+                    const uint32_t pre = hi_part ? (low | acc_hi) : acc_lo;
+                    acc_hi |= hi_part ? c[i] : 0u;
+                    acc_lo |= hi_part ? 0u : c[i];
+                    col[(i + lane) & 31] = pre;
+                }
+            }
+            __syncwarp();
+            uint32_t summ = 0;                      // bit w: word w non-empty
+            for (int w = 0; w < 32; ++w) summ |= bw[32 * w] ? (1u << w) : 0u;
+            for (int t = q0; t < q1; ++t) {
+                const int lr = (int)lrk[t];
+                const int w = lr >> 5, bb = lr & 31;
+                const uint32_t word = bw[32 * w];
+                const uint32_t mlo = word & ((1u << bb) - 1u);
+                const uint32_t mhi = word & ~((2u << bb) - 1u);       // bb = 31: 0
+                const uint32_t slo = summ & ((1u << w) - 1u);
+                const uint32_t shi = summ & ~((2u << w) - 1u);
+                int pl = -1, sl = -1;
+                if (mlo) pl = (w << 5) | (31 - __clz(mlo));
+                else if (slo) { const int ww = 31 - __clz(slo); pl = (ww << 5) | (31 - __clz(bw[32 * ww])); }
+                if (mhi) sl = (w << 5) | (__ffs(mhi) - 1);
+                else if (shi) { const int ww = __ffs(shi) - 1; sl = (ww << 5) | (__ffs(bw[32 * ww]) - 1); }
+                bw[32 * w] = word | (1u << bb);
+                summ |= 1u << w;
+                int2 q = pp[t];
+                if (pl >= 0) q.x = max(q.x, (int)srt[pl]);
+                if (sl >= 0) { const int r = (int)srt[sl]; q.y = q.y < 0 ? r : min(q.y, r); }
+                pp[t] = q;
+            }
+        }
+        __syncthreads();
+        // ranks -> rank nodes of pair b-1 (B's t-th smallest is node jrs[t]);
+        // the run's ranks join W for the next run
+        for (int t = tid; t < len; t += blockDim.x) {
+            const int2 q = pp[t];
+            const uint32_t pv = q.x >= 0 ? __ldg(jrs + q.x) : sentB;
+            const uint32_t nx = q.y >= 0 ? __ldg(jrs + q.y) : sentB;
+            p.ulink[base + i0 + t] = make_uint2(pv, nx);
+            const uint32_t r = rr[t];
+            atomicOr(&W[r >> 5], 1u << (r & 31));
+            atomicOr(&W1[r >> 10], 1u << ((r >> 5) & 31));
+        }
+        __syncthreads();
     }
 }
 
@@ -293,10 +468,12 @@ large_unwind(LargeParams p, const uint32_t* __restrict__ vs, int nw, int ns)
 // nearest marked ranks of its own block, and the small elements are the
 // window's h smallest (Section 6.3 invariant), found by a prefix count.
 __global__ void __launch_bounds__(256)
-large_seginit(LargeParams p, int nw, int ns)
+large_seginit(LargeTable tab)
 {
     extern __shared__ __align__(16) uint32_t sw[];
-    const int64_t sid = blockIdx.x;
+    int64_t sid;
+    const LargeParams p = find_large(tab, kLSeg, blockIdx.x, &sid);
+    const int nw = (2 * p.k + 31) / 32, ns = (nw + 31) / 32;
     const int64_t q = sid / p.S;
     const int s = (int)(sid - q * p.S);
     const int NB = block_len(p, q + 1);
@@ -406,11 +583,13 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr)
 // joint ranks, so "is small" and the peek comparison compare node numbers;
 // the sentinels 2k (A) and 2k+1 (B) rank above every element.
 __global__ void __launch_bounds__(32)
-large_chain(LargeParams p)
+large_chain(LargeTable tab, int64_t items)
 {
     constexpr int kAhead = 8;                      // prefetch distance in steps
-    const int64_t sid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (sid >= p.npairs * p.S) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= items) return;
+    int64_t sid;
+    const LargeParams p = find_large(tab, kLChain, g, &sid);
     const int64_t q = sid / p.S;
     const int s = (int)(sid - q * p.S);
     const int NB = block_len(p, q + 1);
@@ -462,11 +641,13 @@ large_chain(LargeParams p)
 
 template <typename ValT>
 __global__ void __launch_bounds__(256)
-large_epilogue(LargeParams p, const uint32_t* __restrict__ vs)
+large_epilogue(LargeTable tab, int64_t items)
 {
-    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t m = p.n - p.k + 1;
-    if (o >= m) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= items) return;
+    int64_t o;
+    const LargeParams p = find_large(tab, kLEpi, g, &o);
+    const uint32_t* __restrict__ vs = p.vsort;
     int64_t src;
     if (o == 0) {
         src = vs[p.h];                           // y[0] = X_0[P_0[h]]
@@ -507,7 +688,9 @@ static size_t unwind_smem(int k, int* nw, int* ns)
 {
     *nw = (k + 31) / 32;
     *ns = (*nw + 31) / 32;
-    return 4ull * (size_t)(*nw + *ns) + 12ull * kUnwindRun;
+    // pp (8 B), rr, srt, lrk (4 B each) per run position; 32 x 32 local
+    // bitset words; 256 scan counts; W, R, Rc (nw each) and W1 (ns)
+    return 20ull * kUnwindRun + 4ull * (32 * 32 + 256) + 4ull * (3 * (size_t)*nw + *ns);
 }
 static size_t seginit_smem(int k, int* nw, int* ns)
 {
@@ -546,14 +729,15 @@ cudaError_t large_setup()
                                 kMaxSmemBytes);
 }
 
-// All launches of one call; KeyT = uint32_t or uint64_t (key and element width).
+// The launch sequence of one call, for every signal of `tab`: chunk sort,
+// ntier merge tiers, ranks, joint ranks, unwind, segment states, chains,
+// store.  tot[kind] = items of each launch over all signals; the shared
+// memory of the unwind and segment-state CTAs is sized for the largest k.
+// KeyT = uint32_t or uint64_t (key and element width).
 template <typename KeyT>
-static cudaError_t run_large(LargeParams& p, const LargeShape& sh, size_t usmem, int unw, int uns,
-                             size_t ssmem, int snw, int sns, cudaStream_t stream,
-                             LaunchStats* stats)
+static cudaError_t run_large(const LargeTable& tab, const int64_t* tot, int ntier, int kmax,
+                             cudaStream_t stream, LaunchStats* stats)
 {
-    const int k = p.k;
-    const uint64_t kp = (uint64_t)sh.kp;
     auto launched = [&]() -> cudaError_t {
         if (stats) stats->launches += 1;
         return cudaGetLastError();
@@ -566,65 +750,56 @@ static cudaError_t run_large(LargeParams& p, const LargeShape& sh, size_t usmem,
         stats->ring_pos += 1;
     }
     auto mark = [&](int idx) { if (evs) cudaEventRecord(evs[idx], stream); };
+    auto grid = [](int64_t items, int per) { return (unsigned)((items + per - 1) / per); };
+    int unw, uns, snw, sns;
+    const size_t usmem = unwind_smem(kmax, &unw, &uns);
+    const size_t ssmem = seginit_smem(kmax, &snw, &sns);
     cudaError_t e;
     mark(0);
     // phase 1: chunks, then merge tiers (ping-pong between the A and B buffers)
-    const int cpb = (k + kChunk - 1) / kChunk;
-    const int64_t warps = sh.nblocks * cpb;
-    large_chunk_sort<KeyT><<<(unsigned)((warps + 7) / 8), 256, 8 * chunk_warp_bytes<KeyT>(), stream>>>(p, cpb);
+    large_chunk_sort<KeyT><<<grid(tot[kLChunk], 8), 256, 8 * chunk_warp_bytes<KeyT>(), stream>>>(tab, tot[kLChunk]);
     if ((e = launched()) != cudaSuccess) return e;
-    KeyT *ks = (KeyT*)p.keyA, *kt = (KeyT*)p.keyB;
-    uint32_t *vs = p.valA, *vt = p.valB;
-    const int per_block4 = (int)(kp / 4);
-    for (int R = kChunk; R < k; R *= 2) {
-        const int64_t threads = sh.nblocks * per_block4;
-        large_merge<KeyT><<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(p, ks, vs, kt, vt, R, per_block4);
+    for (int t = 0; t < ntier; ++t) {
+        large_merge<KeyT><<<grid(tot[kLMerge0 + t], 256), 256, 0, stream>>>(tab, t, tot[kLMerge0 + t]);
         if ((e = launched()) != cudaSuccess) return e;
-        KeyT* t1 = ks; ks = kt; kt = t1;
-        uint32_t* t2 = vs; vs = vt; vt = t2;
     }
-    if (sh.npairs > 0) {
+    if (tot[kLChain] > 0) {
         // phase 2: ranks, joint ranks, unwind links, segment states, chains
-        const int64_t tr = sh.nblocks * sh.kp;
-        large_ranks<<<(unsigned)((tr + 255) / 256), 256, 0, stream>>>(p, vs);
+        large_ranks<<<grid(tot[kLRanks], 256), 256, 0, stream>>>(tab, tot[kLRanks]);
         if ((e = launched()) != cudaSuccess) return e;
-        const int64_t tj = sh.npairs * 2 * sh.kp;
-        large_jrank<KeyT><<<(unsigned)((tj + 255) / 256), 256, 0, stream>>>(p, ks, vs);
+        large_jrank<KeyT><<<grid(tot[kLJrank], 256), 256, 0, stream>>>(tab, tot[kLJrank]);
         if ((e = launched()) != cudaSuccess) return e;
         mark(1);
-        const dim3 ug((unsigned)(sh.nblocks - 1), (unsigned)((k + kUnwindRun - 1) / kUnwindRun));
-        large_unwind<<<ug, 256, usmem, stream>>>(p, vs, unw, uns);
+        large_unwind<<<(unsigned)tot[kLUnwind], 256, usmem, stream>>>(tab);
         if ((e = launched()) != cudaSuccess) return e;
         mark(2);
-        const int64_t nseg = sh.npairs * sh.S;
-        large_seginit<<<(unsigned)nseg, 256, ssmem, stream>>>(p, snw, sns);
+        large_seginit<<<(unsigned)tot[kLSeg], 256, ssmem, stream>>>(tab);
         if ((e = launched()) != cudaSuccess) return e;
-        large_chain<<<(unsigned)((nseg + 31) / 32), 32, 0, stream>>>(p);
+        large_chain<<<grid(tot[kLChain], 32), 32, 0, stream>>>(tab, tot[kLChain]);
         if ((e = launched()) != cudaSuccess) return e;
     } else {
         mark(1);
         mark(2);
     }
     mark(3);
-    const int64_t m = p.n - k + 1;
-    large_epilogue<KeyT><<<(unsigned)((m + 255) / 256), 256, 0, stream>>>(p, vs);
+    large_epilogue<KeyT><<<grid(tot[kLEpi], 256), 256, 0, stream>>>(tab, tot[kLEpi]);
     if ((e = launched()) != cudaSuccess) return e;
     mark(4);
     return cudaSuccess;
 }
 
-cudaError_t launch_large(const void* x, int64_t n, int k, int rank, Elem el, void* y,
-                         int32_t* argmed, void* ws, size_t ws_bytes, cudaStream_t stream,
-                         LaunchStats* stats)
+// Descriptor of one signal carved from `w` (advanced past its workspace);
+// its items are appended to the running totals tot[].
+static bool large_prepare(LargeParams& p, const void* x, int64_t n, int k, int rank, Elem el,
+                          void* y, int32_t* argmed, char*& w, int64_t* tot)
 {
-    if (k < 1 || k > kLargeMaxK || n < k || rank < 0 || rank >= k) return cudaErrorInvalidValue;
-    if (ws_bytes < large_workspace_bytes(n, k, el.wide)) return cudaErrorInvalidValue;
+    if (k < 1 || k > kLargeMaxK || n < k || rank < 0 || rank >= k) return false;
     int unw, uns, snw, sns;
-    const size_t usmem = unwind_smem(k, &unw, &uns);
-    const size_t ssmem = seginit_smem(k, &snw, &sns);
-    if (usmem > (size_t)kMaxSmemBytes || ssmem > (size_t)kMaxSmemBytes) return cudaErrorInvalidValue;
+    if (unwind_smem(k, &unw, &uns) > (size_t)kMaxSmemBytes ||
+        seginit_smem(k, &snw, &sns) > (size_t)kMaxSmemBytes)
+        return false;
     const LargeShape sh = large_shape(n, k);
-    LargeParams p{};
+    p = LargeParams{};
     p.x = x; p.y = y; p.argmed = argmed;
     p.n = n; p.k = k; p.h = rank;
     p.nblocks = sh.nblocks; p.npairs = sh.npairs; p.kp = sh.kp;
@@ -633,7 +808,7 @@ cudaError_t launch_large(const void* x, int64_t n, int k, int rank, Elem el, voi
     const uint64_t nb = (uint64_t)sh.nblocks, kp = (uint64_t)sh.kp;
     const uint64_t np1 = (uint64_t)(sh.npairs > 0 ? sh.npairs : 1);
     const uint64_t kb = (uint64_t)el.bytes();
-    char* w = (char*)ws;
+    char* const w0 = w;
     p.keyA = w;            w += a256(kb * nb * kp);
     p.keyB = w;            w += a256(kb * nb * kp);
     p.valA = (uint32_t*)w; w += a256(4ull * nb * kp);
@@ -647,8 +822,84 @@ cudaError_t launch_large(const void* x, int64_t n, int k, int rank, Elem el, voi
     p.M = (uint32_t*)w;    w += a256(8ull * np1 * kp);
     p.seg = (int4*)w;      w += a256(16ull * np1 * sh.S);
     p.lists = (uint2*)w;
-    if (el.wide) return run_large<uint64_t>(p, sh, usmem, unw, uns, ssmem, snw, sns, stream, stats);
-    return run_large<uint32_t>(p, sh, usmem, unw, uns, ssmem, snw, sns, stream, stats);
+    w = w0 + large_workspace_bytes(n, k, el.wide);
+    p.cpb = (k + kChunk - 1) / kChunk;
+    p.ntier = 0;
+    while ((kChunk << p.ntier) < k) ++p.ntier;
+    if (p.ntier > kLMaxTiers) return false;
+    p.ksort = p.ntier & 1 ? p.keyB : p.keyA;
+    p.vsort = p.ntier & 1 ? p.valB : p.valA;
+    int64_t cnt[15] = {0};
+    cnt[kLChunk] = sh.nblocks * p.cpb;
+    for (int t = 0; t < p.ntier; ++t) cnt[kLMerge0 + t] = sh.nblocks * (sh.kp / 4);
+    if (sh.npairs > 0) {
+        cnt[kLRanks] = sh.nblocks * sh.kp;
+        cnt[kLJrank] = sh.npairs * 2 * sh.kp;
+        cnt[kLUnwind] = (sh.nblocks - 1) *
+                        (((k + kUnwindRun - 1) / kUnwindRun + kUnwindRunsPerCta - 1) / kUnwindRunsPerCta);
+        cnt[kLSeg] = sh.npairs * sh.S;
+        cnt[kLChain] = sh.npairs * sh.S;
+    }
+    cnt[kLEpi] = n - k + 1;
+    for (int i = 0; i < 15; ++i) { p.start[i] = tot[i]; tot[i] += cnt[i]; }
+    return true;
+}
+
+cudaError_t launch_large(const void* x, int64_t n, int k, int rank, Elem el, void* y,
+                         int32_t* argmed, void* ws, size_t ws_bytes, cudaStream_t stream,
+                         LaunchStats* stats)
+{
+    if (k < 1 || k > kLargeMaxK || n < k) return cudaErrorInvalidValue;
+    if (ws_bytes < large_workspace_bytes(n, k, el.wide)) return cudaErrorInvalidValue;
+    LargeTable tab{};
+    tab.segs = nullptr;
+    tab.nseg = 1;
+    int64_t tot[15] = {0};
+    char* w = (char*)ws;
+    if (!large_prepare(tab.one, x, n, k, rank, el, y, argmed, w, tot)) return cudaErrorInvalidValue;
+    if (el.wide) return run_large<uint64_t>(tab, tot, tab.one.ntier, k, stream, stats);
+    return run_large<uint32_t>(tab, tot, tab.one.ntier, k, stream, stats);
+}
+
+size_t large_batched_workspace_bytes(const int64_t* n, const int32_t* k, int nseg, bool wide)
+{
+    uint64_t b = a256((uint64_t)nseg * sizeof(LargeParams));
+    for (int s = 0; s < nseg; ++s) b += large_workspace_bytes(n[s], k[s], wide);
+    return (size_t)b;
+}
+
+size_t large_descriptor_bytes() { return sizeof(LargeParams); }
+
+cudaError_t launch_large_batched(const void* x, void* y, int32_t* argmed, Elem el,
+                                 const int64_t* x_off, const int64_t* n, const int64_t* y_off,
+                                 const int32_t* k, int nseg, void* ws, size_t ws_bytes,
+                                 void* stage, size_t stage_bytes, cudaStream_t stream,
+                                 LaunchStats* stats)
+{
+    if (nseg <= 0) return cudaSuccess;
+    if (ws_bytes < large_batched_workspace_bytes(n, k, nseg, el.wide)) return cudaErrorInvalidValue;
+    if (stage_bytes < (size_t)nseg * sizeof(LargeParams)) return cudaErrorInvalidValue;
+    LargeParams* host = (LargeParams*)stage;
+    LargeParams* dev = (LargeParams*)ws;
+    char* w = (char*)ws + a256((uint64_t)nseg * sizeof(LargeParams));
+    int64_t tot[15] = {0};
+    int ntier = 0, kmax = 1;
+    const int eb = el.bytes();
+    for (int s = 0; s < nseg; ++s) {
+        if (!large_prepare(host[s], (const char*)x + x_off[s] * eb, n[s], k[s], (k[s] - 1) / 2, el,
+                           (char*)y + y_off[s] * eb, argmed ? argmed + y_off[s] : nullptr, w, tot))
+            return cudaErrorInvalidValue;
+        ntier = max(ntier, host[s].ntier);
+        kmax = max(kmax, k[s]);
+    }
+    cudaError_t e = cudaMemcpyAsync(dev, host, (size_t)nseg * sizeof(LargeParams),
+                                    cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return e;
+    LargeTable tab{};
+    tab.segs = dev;
+    tab.nseg = nseg;
+    if (el.wide) return run_large<uint64_t>(tab, tot, ntier, kmax, stream, stats);
+    return run_large<uint32_t>(tab, tot, ntier, kmax, stream, stats);
 }
 
 }  // namespace mf

@@ -175,6 +175,43 @@ __device__ __forceinline__ uint32_t udiv(uint32_t x, uint64_t magic)
     return (uint32_t)(((uint64_t)x * magic) >> 32);
 }
 
+// Adaptive step (Section 1: an adaptive sort gives an adaptive median
+// filter): 1 when every block of the tile is in ascending order (the stable
+// order is then the position order), 2 when every block is strictly
+// descending (its reverse), else 0.  A probe of one adjacent pair per lane
+// rules both orders out for almost every unordered tile; only when it does
+// not, lane L checks all pairs (e, e + 1) of its 32 elements that lie in one
+// block.  Kept out of line so that its registers do not add to the sort's.
+__device__ __noinline__ int tile_order(const uint32_t* tk, int tile_n, int k, uint64_t kmagic, int lane)
+{
+    if (tile_n <= 0) return 0;
+    const int e0 = 32 * lane;
+    const int pos0 = e0 - (int)udiv((uint32_t)e0, kmagic) * k;      // position of e0 in its block
+    bool asc = true, desc = true;
+    if (e0 + 1 < tile_n && pos0 + 1 < k) {
+        const uint32_t a = tk[e0], b = tk[e0 + 1];
+        asc = a <= b;
+        desc = a > b;
+    }
+    asc = __all_sync(kFull, asc);
+    desc = __all_sync(kFull, desc);
+    if (!asc && !desc) return 0;
+    int pos = pos0;
+    for (int e = e0; e < e0 + 32; ++e) {                // pairs (e, e + 1), the last one into the next run
+        if (e + 1 < tile_n && pos + 1 < k) {
+            const uint32_t a = tk[e], b = tk[e + 1];
+            asc = asc && a <= b;
+            desc = desc && a > b;
+        }
+        pos = pos + 1 == k ? 0 : pos + 1;
+    }
+    asc = __all_sync(kFull, asc);
+    desc = __all_sync(kFull, desc);
+    return asc ? 1 : (desc ? 2 : 0);
+}
+
+// ADAPTIVE: test every tile for ordered blocks first (sort variant 3).
+template <bool ADAPTIVE>
 __global__ void __launch_bounds__(kSortListWarps * 32, 2)
 sortlist_kernel(SegTable tab)
 {
@@ -217,6 +254,7 @@ sortlist_kernel(SegTable tab)
         }
     }
     __syncthreads();
+    const int order = ADAPTIVE ? tile_order(keys + tile_e0, tile_n, k, p.kmagic, lane) : 0;
     uint64_t v[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
@@ -231,7 +269,24 @@ sortlist_kernel(SegTable tab)
     }
     __syncthreads();                                    // keys read before tiles are written
     // ---- 2. warp merge sort of the tile ------------------------------------------
-    if (tile_n > 0) tile_sort(T, v, lane);
+    if (ADAPTIVE && order != 0) {
+        // ordered tile: element (block b, position j) goes to slot b k + j,
+        // or b k + len_b - 1 - j when descending; slots past tile_n get the
+        // padding composites
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int et = 32 * lane + ((i + lane) & 31);
+            int dst = et;
+            if (order == 2 && et < tile_n) {
+                const int blk = (int)(v[i] >> 42), pos = (int)(v[i] & 1023u);
+                dst = blk * k + min(k, tile_n - blk * k) - 1 - pos;
+            }
+            T[tix(dst)] = v[i];
+        }
+        __syncwarp();
+    } else if (tile_n > 0) {
+        tile_sort(T, v, lane);
+    }
     __syncthreads();
 
     // ---- 3. joint ranks of every pair: merge A's and B's runs, A first on ties ---
@@ -585,13 +640,19 @@ size_t sortlist_smem_bytes(int warps)
 
 cudaError_t sortlist_setup()
 {
-    return cudaFuncSetAttribute(sortlist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sortlist_smem_bytes(kSortListWarps));
+    const int bytes = (int)sortlist_smem_bytes(kSortListWarps);
+    cudaError_t e = cudaFuncSetAttribute(sortlist_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sortlist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-cudaError_t launch_sortlist(const SegTable& tab, int64_t items, int warps, cudaStream_t stream)
+cudaError_t launch_sortlist(const SegTable& tab, int64_t items, int warps, bool adaptive,
+                            cudaStream_t stream)
 {
-    sortlist_kernel<<<(unsigned)items, 32 * warps, sortlist_smem_bytes(warps), stream>>>(tab);
+    if (adaptive)
+        sortlist_kernel<true><<<(unsigned)items, 32 * warps, sortlist_smem_bytes(warps), stream>>>(tab);
+    else
+        sortlist_kernel<false><<<(unsigned)items, 32 * warps, sortlist_smem_bytes(warps), stream>>>(tab);
     return cudaGetLastError();
 }
 

@@ -195,3 +195,68 @@ def test_tiers_agree_and_threshold_resets(handle, large_handle):
         assert mf.mf_launch_count(h) - l0 > 4
     finally:
         mf.mf_destroy(h)
+
+
+def _batch(ns, ks, dtype, seed):
+    gen = uniform_i32 if dtype == "int32" else random_walk_f32
+    xs = [gen(n, seed=seed + i) for i, n in enumerate(ns)]
+    if dtype == "int32":
+        xs = [(v % 65536).astype(np.int32) for v in xs]        # many ties at large k
+    x_off = np.cumsum([0] + list(ns[:-1]))
+    ms = [n - k + 1 for n, k in zip(ns, ks)]
+    y_off = np.cumsum([0] + ms[:-1])
+    return xs, np.concatenate(xs), x_off, y_off, ms
+
+
+@pytest.mark.parametrize("dtype", ["float32", "int32"])
+def test_batched_large_signals_share_one_launch_sequence(handle, dtype):
+    """The large-k signals of a batch run in one launch sequence of the
+    global-memory tier: a batch with five of them (ragged, n = k, n = 2k + 1)
+    makes as many launches as one with a single one of the same largest k,
+    and every output equals the signal filtered alone (bit for bit, with
+    argmed)."""
+    small_n, small_k = [4000, 9000, 30000], [31, 255, 1001]
+    one = (small_n + [60_000], small_k + [20_001])
+    five = (small_n + [60_000, 9_345, 2 * 12_001 + 1, 41_003, 80_000],
+            small_k + [20_001, 9_345, 12_001, 16_385, 15_001])
+    counts = []
+    for ns, ks in (one, five):
+        xs, x, x_off, y_off, ms = _batch(ns, ks, dtype, seed=70)
+        xd = torch.from_numpy(x).to(DEV)
+        y = torch.full((sum(ms),), -1, dtype=xd.dtype, device=DEV)
+        a = torch.full((sum(ms),), -1, dtype=torch.int32, device=DEV)
+        segs = mf.make_segments(ns, ks, x_off, y_off)
+        mf.mf_filter_batched(handle, xd, y, segs, a)          # sizes the workspace
+        mf.mf_sync(handle)
+        l0 = mf.mf_launch_count(handle)
+        mf.mf_filter_batched(handle, xd, y, segs, a)
+        mf.mf_sync(handle)
+        counts.append(mf.mf_launch_count(handle) - l0)
+        y_np, a_np = y.cpu().numpy(), a.cpu().numpy().astype(np.int64)
+        for i, (n, k) in enumerate(zip(ns, ks)):
+            sl = slice(int(y_off[i]), int(y_off[i]) + ms[i])
+            ys, as_ = gpu_filter(handle, xs[i], k)
+            assert np.array_equal(bits(y_np[sl]), bits(ys)), (dtype, n, k)
+            assert np.array_equal(a_np[sl], as_), (dtype, n, k)
+    assert counts[0] == counts[1], counts
+
+
+def test_batched_large_signals_against_oracle(handle):
+    """Three large-k signals in one batched call, sampled windows (every pair
+    and chain-segment boundary) against the oracle."""
+    rng = np.random.default_rng(11)
+    ns, ks = [50_000, 30_001, 70_003], [10_001, 15_001, 30_001]
+    xs, x, x_off, y_off, ms = _batch(ns, ks, "float32", seed=90)
+    xd = torch.from_numpy(x).to(DEV)
+    y = torch.full((sum(ms),), -1.0, device=DEV)
+    a = torch.full((sum(ms),), -1, dtype=torch.int32, device=DEV)
+    mf.mf_filter_batched(handle, xd, y, mf.make_segments(ns, ks, x_off, y_off), a)
+    mf.mf_sync(handle)
+    y_np, a_np = y.cpu().numpy(), a.cpu().numpy().astype(np.int64)
+    for i, (n, k) in enumerate(zip(ns, ks)):
+        starts = segment_starts(n, k, rng)
+        ry, ra = oracle.window_medians(xs[i], k, starts)
+        sl = y_np[int(y_off[i]):int(y_off[i]) + ms[i]]
+        al = a_np[int(y_off[i]):int(y_off[i]) + ms[i]]
+        assert np.array_equal(bits(sl[starts]), bits(ry)), (n, k)
+        assert np.array_equal(al[starts], ra), (n, k)

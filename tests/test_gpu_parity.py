@@ -82,6 +82,31 @@ def test_paper_generators(handle, gen, dtype):
         check_full(handle, x, k, f"{gen} {dtype} k={k}")
 
 
+@pytest.mark.parametrize("k", [3, 31, 101, 511, 1001])
+def test_ordered_and_unordered_tiles_mixed(handle, k):
+    """Sort variant 3 skips tiles whose blocks are all ascending (ties kept in
+    position order) or all strictly descending: a signal whose stretches are
+    ascending with repeated values, strictly descending, constant, and random
+    walk, each several tiles long, checked in full against the oracle with
+    that variant and with the default one."""
+    rng = np.random.default_rng(k)
+    span = 5 * 1024 + 77
+    asc = np.sort(rng.integers(0, 50, size=span)).astype(np.float32)          # many ties
+    desc = (np.arange(span, 0, -1, dtype=np.float64) * 0.25 - 300.0).astype(np.float32)
+    const = np.full(span, 7.0, np.float32)
+    x = np.concatenate([asc, desc, random_walk_f32(span, seed=k), const, asc[::-1].copy(),
+                        desc[::-1].copy()])
+    xi = np.ascontiguousarray(x.astype(np.int32))
+    h3 = mf.mf_create(0, torch.cuda.current_stream(DEV))
+    try:
+        mf.mf_set_sort_variant(h3, k, 3)
+        for hh, what in ((h3, "adaptive"), (handle, "default")):
+            check_full(hh, x, k, f"ordered mix {what} k={k}")
+            check_full(hh, xi, k, f"ordered mix int {what} k={k}")
+    finally:
+        mf.mf_destroy(h3)
+
+
 def test_many_tiles_ragged_tail(handle):
     for k in (31, 1001):
         n = 61 * 1001 * 3 + 517

@@ -80,3 +80,51 @@ def test_tier_threshold_tuning_and_reload(tmp_path):
             mf.mf_destroy(h2)
     finally:
         mf.mf_destroy(h)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("k", [31, 255, 1001])
+def test_both_sort_variants_are_exact(variant, k):
+    """Merge-sort tiles (variant 1), the warp radix sort (variant 2) and the
+    adaptive tiles (variant 3) give the same stable order, so the same outputs
+    and argmedians as the oracle."""
+    h = mf.mf_create(0, torch.cuda.current_stream(DEV))
+    try:
+        mf.mf_set_sort_variant(h, k, variant)
+        x_np = random_walk_f32(40_009, seed=k + variant)
+        x = torch.from_numpy(x_np).to(DEV)
+        y = torch.empty(x_np.size - k + 1, device=DEV)
+        a = torch.empty(x_np.size - k + 1, dtype=torch.int32, device=DEV)
+        mf.mf_filter(h, x, k, y, a)
+        mf.mf_sync(h)
+        ry, ra = oracle.median_filter(x_np, k)
+        np.testing.assert_array_equal(y.cpu().numpy().view(np.uint32), ry.view(np.uint32))
+        np.testing.assert_array_equal(a.cpu().numpy().astype(np.int64), ra)
+    finally:
+        mf.mf_destroy(h)
+
+
+def test_tune_batched_applies_choices_and_stays_exact():
+    """Tuning on a batch picks a variant and pairs per CTA for every class the
+    batch holds; the tuned batched call gives the untuned call's bits."""
+    from signals import batched_signals
+    b = batched_signals(nseg=200, seed=12, n_hi=40_000)
+    x = torch.from_numpy(b.x).to(DEV)
+    segs = mf.make_segments(b.n, b.k, b.x_off, b.y_off)
+    h = mf.mf_create(0, torch.cuda.current_stream(DEV))
+    try:
+        y0 = torch.full((b.y_total,), -1.0, device=DEV)
+        mf.mf_filter_batched(h, x, y0, segs)
+        mf.mf_sync(h)
+        res = tune.tune_batched(h, x, segs)
+        present = {next(c for c in tune.CLASS_MAX if k <= c) for k in b.k}
+        assert {int(c) for c in res} == present
+        for c, v in res.items():
+            assert v["sort_variant"] in ((1, 2, 3) if int(c) <= tune.FUSED_MAX_K else (0,))
+            assert v["sort_pairs_per_cta"] in tune.SORT_CANDIDATES
+        y1 = torch.full((b.y_total,), -2.0, device=DEV)
+        mf.mf_filter_batched(h, x, y1, segs)
+        mf.mf_sync(h)
+        assert torch.equal(y0.view(torch.int32), y1.view(torch.int32))
+    finally:
+        mf.mf_destroy(h)
