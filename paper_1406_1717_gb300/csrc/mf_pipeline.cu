@@ -504,75 +504,56 @@ __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<FMT>& L
 }
 
 // The same step for the packed format with one level of shared-memory loads.
-// Every word the step can move m to is a neighbour of m_A or m_B at the start
-// of the step, or a word the step already holds (Section 5.3: delete moves m
-// to prev(m) or, when i = m, to a neighbour of i = m; undelete moves m to
-// prev(m), which is i itself when i is relinked just before m; advance moves
-// m to next(m), and the new m of the step before is always next to the old
-// one).  So the words of prev / next of m_A and of m_B, and of slot i + 1
-// (the next step's A node), are loaded before this step's own relinks, and
-// the relinks' effect on them is applied in registers: unlinking i sets
-// next(pa) from i to na and prev(na) from i to pa; relinking i sets next(pb)
-// from nb to i and prev(nb) from pb to i (equations del / undo-del of
-// Section 4).  A nodes (positions > i, sentinel k) and B nodes (positions
-// < i, sentinel k + 1) are disjoint, so each word takes at most the two
-// patches of its own list.  The next step's loads then depend only on this
-// step's selects, not on a second load.
+// Every node a step can move an m pointer to is m_A, m_B or one of their
+// neighbours at the start of the step (Section 5.3: delete moves m to
+// prev(m), or to a neighbour of i when i = m, and then the next node after
+// it; undelete moves m to prev(m), which is i itself when i is relinked just
+// before m; advance moves m to next(m)).  So the step first does its unlink
+// and relink (equations del / undo-del of Section 4), then loads the words of
+// m_A, m_B, their neighbours at the start of the step and slot i + 1 (the next
+// step's A node): the loads see the new links, and their addresses depend
+// only on the state at the start of the step, so they form a single level and
+// the selects that follow need no second load.  (When i = m_A, slot i already
+// holds B's word; the selects do not use m_A's word then.)
 __device__ __forceinline__ uint32_t pair_step_packed(PairState& st, const Lists<kFmtPacked>& L,
-                                                     uint32_t i, uint32_t wa, uint32_t wbw,
-                                                     uint32_t* wnext)
+                                                           uint32_t i, uint32_t wa, uint32_t wbw,
+                                                           uint32_t* wnext)
 {
     using LL = Lists<kFmtPacked>;
-    // -------- loads, all issued before this step's stores ----------------------
     const uint32_t pm = LL::prv(st.wmA), nm = LL::nxt(st.wmA);
     const uint32_t pmB = LL::prv(st.wmB), nmB = LL::nxt(st.wmB);
-    uint32_t wpm = L.ld(pm), wnm = L.ld(nm), wpmB = L.ld(pmB), wnmB = L.ld(nmB);
-    uint32_t wn = L.ld(i + 1);
-    // -------- delete(A, i): unlink, then the patches of the A words ------------
+    // -------- relinks: delete(A, i), undelete(B, i) --------------------------------
     const uint32_t pa = LL::prv(wa), na = LL::nxt(wa), ra = wa >> 20;
+    const uint32_t pb = LL::prv(wbw), nb = LL::nxt(wbw), rb = wbw >> 20;
     L.xr(pa, na ^ i);                                   // next[prev[i]] <- next[i]
     L.xr(na, (pa ^ i) << 10);                           // prev[next[i]] <- prev[i]
-    const uint32_t dnx = i ^ na, dpv = (i ^ pa) << 10;
-    const uint32_t wmA = st.wmA ^ (pa == st.mA ? dnx : 0u) ^ (na == st.mA ? dpv : 0u);
-    wpm ^= (pa == pm ? dnx : 0u) ^ (na == pm ? dpv : 0u);
-    wnm ^= (pa == nm ? dnx : 0u) ^ (na == nm ? dpv : 0u);
-    wn ^= (pa == i + 1 ? dnx : 0u) ^ (na == i + 1 ? dpv : 0u);
-    *wnext = wn;
+    L.st(i, wbw);
+    L.xr(pb, nb ^ i);                                   // next[prev[i]] <- i
+    L.xr(nb, (pb ^ i) << 10);                           // prev[next[i]] <- i
+    // -------- the candidates' words, after the relinks ------------------------
+    const uint32_t wmA = L.ld(st.mA), wpm = L.ld(pm), wnm = L.ld(nm);
+    const uint32_t wmB = L.ld(st.mB), wpmB = L.ld(pmB), wnmB = L.ld(nmB);
+    *wnext = L.ld(i + 1);
+    // -------- delete(A, i): the m pointer and s -----------------------------------
     const bool small = ra < st.rmA;                     // alpha[i] small (or m at the end)
     const bool isM = i == st.mA;
     const bool sApos = st.sA > 0;
-    // large and s > 0: m <- prev[m] (when i = m, next then prev: pa = pm);
-    // large, s = 0 and i = m: m <- next[m] = na = nm; otherwise m stays
     const bool toP = !small && sApos, toN = !small && !sApos && isM;
     const uint32_t mA1 = toP ? pm : (toN ? nm : st.mA);
     const uint32_t wA1 = toP ? wpm : (toN ? wnm : wmA);
     st.sA -= (small || sApos) ? 1 : 0;                  // s <- max(0, s - 1)
-    // next(m) after the delete, for the advance: m unchanged (i small) -> nm;
-    // m <- pm with i = m -> next(pa) = na = nm; m <- pm otherwise -> old m
     const bool nxtOld = toP && !isM;
     const uint32_t aNode = nxtOld ? st.mA : nm, aWord = nxtOld ? wmA : wnm;
-    // -------- undelete(B, i): relink, then the patches of the B words ---------
-    const uint32_t pb = LL::prv(wbw), nb = LL::nxt(wbw), rb = wbw >> 20;
-    L.st(i, wbw);
-    L.xr(pb, nb ^ i);                                   // next[prev[i]] <- i
-    L.xr(nb, (pb ^ i) << 10);                           // prev[next[i]] <- i
-    const uint32_t enx = nb ^ i, epv = (pb ^ i) << 10;
-    const uint32_t wmB = st.wmB ^ (pb == st.mB ? enx : 0u) ^ (nb == st.mB ? epv : 0u);
-    wpmB ^= (pb == pmB ? enx : 0u) ^ (nb == pmB ? epv : 0u);
-    wnmB ^= (pb == nmB ? enx : 0u) ^ (nb == nmB ? epv : 0u);
+    // -------- undelete(B, i): the m pointer ---------------------------------------
     const bool smallB = rb < st.rmB;                    // small: m <- prev[m]
     const bool justB = nb == st.mB;                     // i relinked just before m
     const uint32_t mB1 = smallB ? (justB ? i : pmB) : st.mB;
     const uint32_t wB1 = smallB ? (justB ? wbw : wpmB) : wmB;
-    // next(m) after the undelete: m moved back -> the old m; else next(m),
-    // which is i when i was relinked just after m
     const bool afterB = pb == st.mB;
     const uint32_t bNode = smallB ? st.mB : (afterB ? i : nmB);
     const uint32_t bWord = smallB ? wmB : (afterB ? wbw : wnmB);
     // -------- advance the list whose first large element is smaller -----------
-    // (s_A was positive before the delete <=> s_A + s_B < h now; eq. inv)
-    const uint32_t rA1 = wA1 >> 20, rB1 = wB1 >> 20;
-    const bool aA = rA1 < rB1;                          // peek(A) <= peek(B): A first on ties
+    const bool aA = (wA1 >> 20) < (wB1 >> 20);          // peek(A) <= peek(B): A first on ties
     const bool advA = sApos && aA, advB = sApos && !aA;
     st.mA = advA ? aNode : mA1;
     st.wmA = advA ? aWord : wA1;
