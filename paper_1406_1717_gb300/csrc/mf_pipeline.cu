@@ -425,85 +425,13 @@ struct PairState {
     int sA;                   // s_B = h - s_A at every step boundary
 };
 
-// One step i of the post-processing (Section 6.2), branch-free: delete(A, i),
-// undelete(B, i), advance if s_A + s_B < h, return the printed node
-// (isB << 15 | slot).  wa is slot i's current word (loaded after the previous
-// step's last store); the next step's word is loaded into *wnext.  B's
-// position i comes back with the links pb / nb that unwind(B) left it and
-// joint rank rb; wbw is its list word make(pb, nb, rb).
-template <int FMT>
-__device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<FMT>& L, uint32_t i,
-                                              uint32_t wa, uint32_t pb, uint32_t nb, uint32_t rb,
-                                              uint32_t wbw, uint32_t* wnext)
-{
-    using LL = Lists<FMT>;
-    constexpr bool PACKED = LL::PACKED;
-    // -------- delete(A, i) ----------------------------------------------------
-    const uint32_t pa = LL::prv(wa), na = LL::nxt(wa);
-    const uint32_t ra = L.rank(i, wa);
-    L.set_next(pa, na, i);                              // next[prev[i]] <- next[i]
-    L.set_prev(na, pa, i);                              // prev[next[i]] <- prev[i]
-    st.wmA ^= (pa == st.mA) ? (i ^ na) : 0u;            // keep m's cached word exact
-    st.wmA ^= (na == st.mA) ? ((i ^ pa) << LL::PSH) : 0u;
-    if (PACKED) st.rmA = st.wmA >> 20;
-    const bool small = ra < st.rmA;                     // alpha[i] small (or m at the end)
-    const bool isM = (i == st.mA);
-    const bool sApos = st.sA > 0;
-    // large & m == i: m <- next, then prev if s > 0  => pa (s > 0) or na
-    // large & m != i & s > 0: m <- prev[m]
-    const uint32_t tA = isM ? (sApos ? pa : na) : LL::prv(st.wmA);
-    const bool chgA = !small && (isM || sApos);
-    const uint32_t wtA = L.ld(tA);
-    uint32_t rtA = 0;
-    if (!PACKED) rtA = L.rank(tA, wtA);
-    st.mA = chgA ? tA : st.mA;
-    st.wmA = chgA ? wtA : st.wmA;
-    if (PACKED) st.rmA = st.wmA >> 20; else st.rmA = chgA ? rtA : st.rmA;
-    st.sA -= (small || sApos) ? 1 : 0;                  // s <- max(0, s - 1)
-    // -------- undelete(B, i) ----------------------------------------------------
-    L.st(i, wbw);                                       // wbw = make(pb, nb, rb)
-    if (!PACKED) L.set_rank(i, rb);
-    L.set_next(pb, i, nb);                              // next[prev[i]] <- i
-    L.set_prev(nb, i, pb);                              // prev[next[i]] <- i
-    st.wmB ^= (pb == st.mB) ? (nb ^ i) : 0u;
-    st.wmB ^= (nb == st.mB) ? ((pb ^ i) << LL::PSH) : 0u;
-    const bool smallB = rb < st.rmB;                    // small: m <- prev[m]
-    const uint32_t tB = LL::prv(st.wmB);
-    const uint32_t wtB = L.ld(tB);
-    uint32_t rtB = 0;
-    if (!PACKED) rtB = L.rank(tB, wtB);
-    *wnext = L.ld(i + 1);                               // all of step i's stores are issued
-    st.mB = smallB ? tB : st.mB;
-    st.wmB = smallB ? wtB : st.wmB;
-    if (PACKED) st.rmB = st.wmB >> 20; else st.rmB = smallB ? rtB : st.rmB;
-    // -------- advance the list whose first large element is smaller -----------
-    // s_A + s_B = h before the step (eq. inv, Section 6.3); delete(A, i) lowers
-    // s_A exactly when S_A was not empty, and undelete leaves s_B, so the
-    // test "s_A + s_B < h" is "s_A was positive before the delete"
-    const bool adv = sApos;
-    const bool aA = st.rmA < st.rmB;                    // peek(A) <= peek(B): A first on ties
-    const uint32_t tN = aA ? LL::nxt(st.wmA) : LL::nxt(st.wmB);
-    const uint32_t wN = L.ld(tN);
-    uint32_t rN = 0;
-    if (!PACKED) rN = L.rank(tN, wN);
-    const bool advA = adv && aA, advB = adv && !aA;
-    st.mA = advA ? tN : st.mA;
-    st.wmA = advA ? wN : st.wmA;
-    st.mB = advB ? tN : st.mB;
-    st.wmB = advB ? wN : st.wmB;
-    if (PACKED) {
-        st.rmA = st.wmA >> 20;
-        st.rmB = st.wmB >> 20;
-    } else {
-        st.rmA = advA ? rN : st.rmA;
-        st.rmB = advB ? rN : st.rmB;
-    }
-    st.sA += advA ? 1 : 0;
-    // -------- print min(peek(A), peek(B)) ------------------------------------
-    return st.rmA < st.rmB ? st.mA : (0x8000u | st.mB);
-}
-
-// The same step for the packed format with one level of shared-memory loads.
+// One step i of the post-processing (Section 6.2): delete(A, i), undelete(B,
+// i), advance if s_A + s_B < h, and the printed node (isB << 15 | slot) of
+// min(peek A, peek B).  wa is slot i's current word (loaded by the step
+// before); the next step's word comes back in *wnext.  B's position i comes
+// with the links pb / nb that unwind(B) left it and its joint rank rb; wbw is
+// its list word make(pb, nb, rb).
+//
 // Every node a step can move an m pointer to is m_A, m_B or one of their
 // neighbours at the start of the step (Section 5.3: delete moves m to
 // prev(m), or to a neighbour of i when i = m, and then the next node after
@@ -516,8 +444,8 @@ __device__ __forceinline__ uint32_t pair_step(PairState& st, const Lists<FMT>& L
 // the selects that follow need no second load.  (When i = m_A, slot i already
 // holds B's word; the selects do not use m_A's word then.)
 __device__ __forceinline__ uint32_t pair_step_packed(PairState& st, const Lists<kFmtPacked>& L,
-                                                           uint32_t i, uint32_t wa, uint32_t wbw,
-                                                           uint32_t* wnext)
+                                                     uint32_t i, uint32_t wa, uint32_t wbw,
+                                                     uint32_t* wnext)
 {
     using LL = Lists<kFmtPacked>;
     const uint32_t pm = LL::prv(st.wmA), nm = LL::nxt(st.wmA);
@@ -561,6 +489,73 @@ __device__ __forceinline__ uint32_t pair_step_packed(PairState& st, const Lists<
     st.wmB = advB ? bWord : wB1;
     st.rmA = st.wmA >> 20;
     st.rmB = st.wmB >> 20;
+    st.sA += advA ? 1 : 0;
+    // -------- print min(peek(A), peek(B)) ------------------------------------
+    return st.rmA < st.rmB ? st.mA : (0x8000u | st.mB);
+}
+
+// The one-level step of pair_step_packed for the mid and wide formats, whose
+// ranks live (partly) outside the word: after the unlink and relink, the
+// words of m_A, m_B, their neighbours at the start of the step and slot
+// i + 1 are loaded together with the side-array ranks of the neighbours and
+// of slot i + 1 (the m pointers' own ranks do not change: only slot i changes
+// owner).  ra is slot i's rank, loaded by the step before with its word.
+template <int FMT>
+__device__ __forceinline__ uint32_t pair_step_after(PairState& st, const Lists<FMT>& L, uint32_t i,
+                                                    uint32_t wa, uint32_t ra, uint32_t pb, uint32_t nb,
+                                                    uint32_t rb, uint32_t* wnext, uint32_t* rnext)
+{
+    using LL = Lists<FMT>;
+    const uint32_t pm = LL::prv(st.wmA), nm = LL::nxt(st.wmA);
+    const uint32_t pmB = LL::prv(st.wmB), nmB = LL::nxt(st.wmB);
+    // -------- relinks: delete(A, i), undelete(B, i) --------------------------------
+    const uint32_t pa = LL::prv(wa), na = LL::nxt(wa);
+    const uint32_t wbw = LL::make(pb, nb, rb);
+    L.set_next(pa, na, i);                              // next[prev[i]] <- next[i]
+    L.set_prev(na, pa, i);                              // prev[next[i]] <- prev[i]
+    L.st(i, wbw);
+    L.set_rank(i, rb);
+    L.set_next(pb, i, nb);                              // next[prev[i]] <- i
+    L.set_prev(nb, i, pb);                              // prev[next[i]] <- i
+    // -------- the candidates' words and ranks, after the relinks -----------------
+    const uint32_t wmA = L.ld(st.mA), wpm = L.ld(pm), wnm = L.ld(nm);
+    const uint32_t wmB = L.ld(st.mB), wpmB = L.ld(pmB), wnmB = L.ld(nmB);
+    const uint32_t wn = L.ld(i + 1);
+    const uint32_t rpm = L.rank(pm, wpm), rnm = L.rank(nm, wnm);
+    const uint32_t rpmB = L.rank(pmB, wpmB), rnmB = L.rank(nmB, wnmB);
+    *wnext = wn;
+    *rnext = L.rank(i + 1, wn);
+    // -------- delete(A, i): the m pointer and s -----------------------------------
+    const bool small = ra < st.rmA;                     // alpha[i] small (or m at the end)
+    const bool isM = i == st.mA;
+    const bool sApos = st.sA > 0;
+    const bool toP = !small && sApos, toN = !small && !sApos && isM;
+    const uint32_t mA1 = toP ? pm : (toN ? nm : st.mA);
+    const uint32_t wA1 = toP ? wpm : (toN ? wnm : wmA);
+    const uint32_t rA1 = toP ? rpm : (toN ? rnm : st.rmA);
+    st.sA -= (small || sApos) ? 1 : 0;                  // s <- max(0, s - 1)
+    const bool nxtOld = toP && !isM;
+    const uint32_t aNode = nxtOld ? st.mA : nm, aWord = nxtOld ? wmA : wnm;
+    const uint32_t aRank = nxtOld ? st.rmA : rnm;
+    // -------- undelete(B, i): the m pointer ---------------------------------------
+    const bool smallB = rb < st.rmB;                    // small: m <- prev[m]
+    const bool justB = nb == st.mB;                     // i relinked just before m
+    const uint32_t mB1 = smallB ? (justB ? i : pmB) : st.mB;
+    const uint32_t wB1 = smallB ? (justB ? wbw : wpmB) : wmB;
+    const uint32_t rB1 = smallB ? (justB ? rb : rpmB) : st.rmB;
+    const bool afterB = pb == st.mB;
+    const uint32_t bNode = smallB ? st.mB : (afterB ? i : nmB);
+    const uint32_t bWord = smallB ? wmB : (afterB ? wbw : wnmB);
+    const uint32_t bRank = smallB ? st.rmB : (afterB ? rb : rnmB);
+    // -------- advance the list whose first large element is smaller -----------
+    const bool aA = rA1 < rB1;                          // peek(A) <= peek(B): A first on ties
+    const bool advA = sApos && aA, advB = sApos && !aA;
+    st.mA = advA ? aNode : mA1;
+    st.wmA = advA ? aWord : wA1;
+    st.rmA = advA ? aRank : rA1;
+    st.mB = advB ? bNode : mB1;
+    st.wmB = advB ? bWord : wB1;
+    st.rmB = advB ? bRank : rB1;
     st.sA += advA ? 1 : 0;
     // -------- print min(peek(A), peek(B)) ------------------------------------
     return st.rmA < st.rmB ? st.mA : (0x8000u | st.mB);
@@ -625,6 +620,7 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
     uint4 v0 = u0, v1 = u1, kv = jv;
     if (nch > 1) { v0 = __ldg(ul4 + 2); v1 = __ldg(ul4 + 3); kv = __ldg(jb4 + 1); }
     uint32_t wa = L.ld(0);
+    uint32_t ra = L.rank(0, wa);
     for (int c = 0; c < nch; ++c) {
         uint4 x0 = v0, x1 = v1, xv = kv;
         if (c + 2 < nch) {
@@ -643,10 +639,13 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
                 uint32_t wn;
                 const uint32_t pb = wbv[t] >> 16, nb = wbv[t] & 0xffffu;
                 uint32_t o;
-                if constexpr (PACKED)
+                if constexpr (PACKED) {
                     o = pair_step_packed(st, L, (uint32_t)i, wa, LL::make(pb, nb, rb), &wn);
-                else
-                    o = pair_step<FMT>(st, L, (uint32_t)i, wa, pb, nb, rb, LL::make(pb, nb, rb), &wn);
+                } else {
+                    uint32_t rn;
+                    o = pair_step_after<FMT>(st, L, (uint32_t)i, wa, ra, pb, nb, rb, &wn, &rn);
+                    ra = rn;
+                }
                 wa = wn;
                 ov[t >> 1] |= (t & 1) ? (o << 16) : o;
             }
