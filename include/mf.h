@@ -238,13 +238,15 @@ mf_status mf_set_tuning(mf_handle h, int32_t k, int32_t sort_pairs_per_cta,
  *  0  built-in choice;
  *  1  merge-sort tiles: a warp sorts 1024-element tiles (odd-even network per
  *     lane, merge-path rounds) in the same kernel that builds both lists
- *     (4-byte elements with k <= 1021; elsewhere variant 2 is used);
+ *     (k <= 1021; elsewhere variant 2 is used); 8-byte elements are sorted
+ *     twice, on the low then the high half of their 64-bit key;
  *  2  warp LSD radix sort (8-bit digits) in a kernel of its own, followed by
  *     separate unwind, chain and store kernels;
  *  3  as 1, but every tile is first tested for blocks that are already in
  *     order (ascending, or strictly descending) and those tiles are not
  *     sorted (Section 1: an adaptive sort gives an adaptive median filter);
- *     the test costs a few percent on unordered input.
+ *     the test costs a few percent on unordered input (4-byte elements;
+ *     for 8-byte elements 3 acts as 1).
  * Used by the autotuner.  Errors: MF_ERR_NULL, MF_ERR_K_GT_N (k < 1),
  * MF_ERR_UNSUPPORTED (variant outside 0 .. 3). */
 mf_status mf_set_sort_variant(mf_handle h, int32_t k, int32_t variant);
@@ -279,7 +281,7 @@ mf_status mf_get_tier_threshold(mf_handle h, int32_t* k_large_from);
  * mf_filter_host call records CUDA events on the handle's stream around its
  * four kernel groups (sort, unwind, post-processing chains, store), in a ring
  * of the last 128 calls; enabling resets the ring.  The groups per path:
- *   4-byte elements, k <= 1021: the fused sort kernel (block sort, joint
+ *   k <= 1021: the fused sort kernel (block sort, joint
  *     ranks, unwind links, list words) / nothing / chains / store;
  *   other windows of the shared-memory pipeline: sort + joint ranks /
  *     unwind links / chains / store;

@@ -25,7 +25,7 @@ struct PipeParams {
     uint16_t* ja;             // [npairs][kp] joint rank of A's position p
     uint16_t* jb;             // [npairs][kp] joint rank of B's position p
     uint16_t* out;            // [npairs][kp] printed node at step i: isB << 15 | slot
-    // fused path (sortlist_kernel; 4-byte elements, k <= kFusedMaxK)
+    // fused path (sortlist_kernel; k <= kFusedMaxK)
     uint32_t* wA;             // [npairs][kw] list words of construct(A): slots 0..k+1, m_A in slot k+2
     uint32_t* wB;             // [npairs][kw] undelete(B, i) word of every position i of B
     int kw;                   // row stride of wA / wB in words: >= k + 3, multiple of 4
@@ -49,9 +49,9 @@ struct Tuning {
     int sort_G;               // pairs per sortmerge CTA
     int epi_G;                // pairs per epilogue CTA
     int variant;              // block sort: 0 built-in, 1 merge-sort tiles (fused path,
-                              // 4-byte elements, k <= kFusedMaxK), 2 warp radix sort
-                              // (four-kernel path), 3 merge-sort tiles that skip
-                              // tiles of ordered blocks
+                              // k <= kFusedMaxK), 2 warp radix sort (four-kernel
+                              // path), 3 merge-sort tiles that skip tiles of
+                              // ordered blocks (4-byte elements; 8-byte: as 1)
 };
 struct SortPlan {
     uint32_t off_keyA, off_keyB, off_valA, off_valB, off_hist;
@@ -105,7 +105,7 @@ struct Elem {
 int pipeline_max_k(bool wide = false);
 size_t sortlist_smem_bytes(int warps);
 cudaError_t sortlist_setup();
-cudaError_t launch_sortlist(const SegTable& tab, int64_t items, int warps, bool adaptive,
+cudaError_t launch_sortlist(const SegTable& tab, int64_t items, int warps, bool adaptive, bool wide,
                             cudaStream_t stream);
 size_t pipeline_workspace_bytes(int64_t n, int k);
 cudaError_t pipeline_setup();

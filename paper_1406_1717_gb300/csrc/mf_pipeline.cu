@@ -1241,9 +1241,10 @@ static bool make_class_plan(int kmax, int64_t total_pairs, int num_sms, const Tu
     const int cls = tune_class_of(kmax);
     if (tune) tune += cls;
     const int64_t want = (total_pairs + 2ll * num_sms - 1) / (2ll * num_sms);
-    // fused path: 4-byte elements whose lists fit the packed chain format
-    c->fused = !wide && kmax <= kFusedMaxK && !(tune && tune->variant == 2);
-    c->adaptive = c->fused && tune && tune->variant == 3;
+    // fused path: lists that fit the packed chain format (4- and 8-byte
+    // elements; the ordered-tile test serves 4-byte keys only)
+    c->fused = kmax <= kFusedMaxK && !(tune && tune->variant == 2);
+    c->adaptive = c->fused && !wide && tune && tune->variant == 3;
     c->lwarps = kSortListWarps;
     c->lGcap = 1 << 30;
     if (tune && tune->sort_G > 0) c->lGcap = tune->sort_G;
@@ -1319,7 +1320,7 @@ static cudaError_t launch_classes(const ClassPlan* cls, const SegTable* tabs, co
     for (int c = 0; c < ncls; ++c) {
         if (cls[c].fused) {
             if ((e = launch_sortlist(tabs[c], tot[c][kItemSort], cls[c].lwarps, cls[c].adaptive,
-                                     stream)) != cudaSuccess)
+                                     cls[c].wide, stream)) != cudaSuccess)
                 return e;
             if (stats) stats->launches += 1;
             continue;

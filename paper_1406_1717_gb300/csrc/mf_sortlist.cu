@@ -1,6 +1,6 @@
-// mf_sortlist.cu -- the fused front half of the pipeline for 4-byte elements
-// and k <= kFusedMaxK: piecewise sort, joint ranks, unwind links and the list
-// words of both block data structures of every pair, in one kernel.
+// mf_sortlist.cu -- the fused front half of the pipeline for k <= kFusedMaxK:
+// piecewise sort, joint ranks, unwind links and the list words of both block
+// data structures of every pair, in one kernel.
 //
 // Paper: "Median Filtering is Equivalent to Sorting" (Suomela).
 //   * stable block sort ........ Section 3 "Piecewise Sorting", Section 5.2:
@@ -24,7 +24,9 @@
 // every block of the tile at once:
 //   1. every lane sorts 32 composites in registers (Batcher's odd-even merge
 //      sorting network, 191 compare-exchanges);
-//   2. five merge-path rounds in shared memory merge the 32 runs to one;
+//   2. five merge-path rounds in shared memory merge the 32 runs to one
+//      (8-byte elements: steps 1-2 twice, on the low then the high half of
+//      the key, the second time with the first sort's rank in the low field);
 //   3. per pair, lanes merge A's and B's sorted runs by key (A first on ties)
 //      and record each element's joint rank;
 //   4. per block of the tile: perm / rank in place of the tile; as A, the list
@@ -210,8 +212,29 @@ __device__ __noinline__ int tile_order(const uint32_t* tk, int tile_n, int k, ui
     return asc ? 1 : (desc ? 2 : 0);
 }
 
+// Key comparison of the pair merges: is A's element (composite ca, CTA
+// element ea) at or before B's (cb, eb) in the window order (A first on equal
+// keys)?  4-byte keys are whole in the composites; 8-byte keys carry their
+// high half there, and equal high halves are decided by the low halves read
+// from x.
+template <bool WIDE>
+__device__ __forceinline__ bool a_first(uint64_t ca, uint64_t cb, const void* x, int64_t ea,
+                                        int64_t eb, bool is_float)
+{
+    const uint32_t ka = comp_key(ca), kb = comp_key(cb);
+    if (!WIDE || ka != kb) return ka <= kb;
+    const uint64_t* x64 = reinterpret_cast<const uint64_t*>(x);
+    return (uint32_t)to_key(__ldg(x64 + ea), is_float) <= (uint32_t)to_key(__ldg(x64 + eb), is_float);
+}
+
 // ADAPTIVE: test every tile for ordered blocks first (sort variant 3).
-template <bool ADAPTIVE>
+// WIDE: 8-byte elements (int64, float64).  The 64-bit order key does not fit
+// a composite, so the tile is sorted twice, least significant half first (a
+// stable LSD sort on two 32-bit digits): by (block, low half, position), then
+// by (block, high half, rank after the first sort).  The first sort's
+// permutation and its inverse stay in the warp's 4 KB of joint-rank space,
+// which the pair merges only use later.
+template <bool ADAPTIVE, bool WIDE>
 __global__ void __launch_bounds__(kSortListWarps * 32, 2)
 sortlist_kernel(SegTable tab)
 {
@@ -236,25 +259,42 @@ sortlist_kernel(SegTable tab)
     const int tile_n = max(0, min(bpw * k, E - tile_e0));
 
     // ---- 1. keys of the CTA's span (coalesced), then 32 composites per lane ----
-    // E <= 32 * blockDim.x: each thread issues its loads 16 at a time
+    // E <= 32 * blockDim.x: each thread issues its loads 16 at a time.  The
+    // composites take the key's low 32 bits (the whole key of 4-byte elements)
     uint32_t* keys = reinterpret_cast<uint32_t*>(smem);
-    const uint32_t* xp = reinterpret_cast<const uint32_t*>(p.x) + ebase;
+    uint64_t* keys64 = reinterpret_cast<uint64_t*>(smem);
 #pragma unroll 1
     for (int i0 = 0; i0 < 32; i0 += 16) {
-        uint32_t raw[16];
+        if constexpr (WIDE) {
+            const uint64_t* xp = reinterpret_cast<const uint64_t*>(p.x) + ebase;
+            uint64_t raw[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int e = tid + (i0 + i) * (int)blockDim.x;
-            raw[i] = e < E ? __ldg(xp + e) : 0u;
-        }
+            for (int i = 0; i < 16; ++i) {
+                const int e = tid + (i0 + i) * (int)blockDim.x;
+                raw[i] = e < E ? __ldg(xp + e) : 0ull;
+            }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int e = tid + (i0 + i) * (int)blockDim.x;
-            if (e < E) keys[e] = to_key(raw[i], p.is_float);
+            for (int i = 0; i < 16; ++i) {
+                const int e = tid + (i0 + i) * (int)blockDim.x;
+                if (e < E) keys64[e] = to_key(raw[i], p.is_float);
+            }
+        } else {
+            const uint32_t* xp = reinterpret_cast<const uint32_t*>(p.x) + ebase;
+            uint32_t raw[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int e = tid + (i0 + i) * (int)blockDim.x;
+                raw[i] = e < E ? __ldg(xp + e) : 0u;
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int e = tid + (i0 + i) * (int)blockDim.x;
+                if (e < E) keys[e] = to_key(raw[i], p.is_float);
+            }
         }
     }
     __syncthreads();
-    const int order = ADAPTIVE ? tile_order(keys + tile_e0, tile_n, k, p.kmagic, lane) : 0;
+    const int order = (ADAPTIVE && !WIDE) ? tile_order(keys + tile_e0, tile_n, k, p.kmagic, lane) : 0;
     uint64_t v[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
@@ -263,7 +303,8 @@ sortlist_kernel(SegTable tab)
         if (et < tile_n) {
             const uint32_t blk = udiv((uint32_t)et, p.kmagic);
             const uint32_t pos = (uint32_t)et - blk * (uint32_t)k;
-            c = ((uint64_t)blk << 42) | ((uint64_t)keys[tile_e0 + et] << 10) | pos;
+            const uint32_t key = WIDE ? (uint32_t)keys64[tile_e0 + et] : keys[tile_e0 + et];
+            c = ((uint64_t)blk << 42) | ((uint64_t)key << 10) | pos;
         }
         v[i] = c;
     }
@@ -287,6 +328,49 @@ sortlist_kernel(SegTable tab)
     } else if (tile_n > 0) {
         tile_sort(T, v, lane);
     }
+    if (WIDE && tile_n > 0) {
+        // second digit: perm1[t] = tile element at rank t after the first
+        // sort, r1[e] = its inverse (16-bit, in this warp's 4 KB after the tiles)
+        uint16_t* perm1 = reinterpret_cast<uint16_t*>(smem + (size_t)W * kTileBytes) + (size_t)warp * 2048;
+        uint16_t* r1 = perm1 + 1024;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int t = lane + 32 * i;
+            const uint64_t c = T[tix(t)];
+            if (t < tile_n) {
+                const int e = (int)(c >> 42) * k + (int)(c & 1023u);
+                perm1[t] = (uint16_t)e;
+                r1[e] = (uint16_t)t;
+            }
+        }
+        __syncwarp();
+        // composites (block : high half : r1), the high halves read again from x
+        const uint64_t* xt = reinterpret_cast<const uint64_t*>(p.x) + ebase + tile_e0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int et = 32 * lane + ((i + lane) & 31);
+            uint64_t c = kPadComp;
+            if (et < tile_n) {
+                const uint32_t blk = udiv((uint32_t)et, p.kmagic);
+                const uint32_t hi = (uint32_t)(to_key(__ldg(xt + et), p.is_float) >> 32);
+                c = ((uint64_t)blk << 42) | ((uint64_t)hi << 10) | r1[et];
+            }
+            v[i] = c;
+        }
+        __syncwarp();
+        tile_sort(T, v, lane);
+        // the low field back from first-sort rank to position in the block
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int x = lane + 32 * i;
+            const uint64_t c = T[tix(x)];
+            if (x < tile_n) {
+                const int e = perm1[c & 1023u];
+                T[tix(x)] = (c & ~1023ull) | (uint64_t)(e - (int)(c >> 42) * k);
+            }
+        }
+        __syncwarp();
+    }
     __syncthreads();
 
     // ---- 3. joint ranks of every pair: merge A's and B's runs, A first on ties ---
@@ -306,10 +390,12 @@ sortlist_kernel(SegTable tab)
             const uint64_t* TA = tiles + (size_t)tA * kTileU64;
             const uint64_t* TB = tiles + (size_t)tB * kTileU64;
             const int offA = (g - tA * bpw) * k, offB = (g + 1 - tB * bpw) * k;
+            const int64_t eA = ebase + (int64_t)g * k, eB = eA + k;      // blocks A and B in x
             int lo = max(0, o0 - NB), hi = min(o0, k);
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (comp_key(TA[tix(offA + mid)]) <= comp_key(TB[tix(offB + o0 - 1 - mid)])) lo = mid + 1;
+                const uint64_t cA = TA[tix(offA + mid)], cB = TB[tix(offB + o0 - 1 - mid)];
+                if (a_first<WIDE>(cA, cB, p.x, eA + comp_pos(cA), eB + comp_pos(cB), p.is_float)) lo = mid + 1;
                 else hi = mid;
             }
             int ia = lo, ib = o0 - lo;
@@ -318,7 +404,8 @@ sortlist_kernel(SegTable tab)
             uint16_t* ja = jaS + (size_t)g * k;
             uint16_t* jb = jbS + (size_t)g * k;
             for (int o = o0; o < o1; ++o) {
-                const bool ta = ib >= NB || (ia < k && comp_key(ca) <= comp_key(cb));
+                const bool ta = ib >= NB ||
+                                (ia < k && a_first<WIDE>(ca, cb, p.x, eA + comp_pos(ca), eB + comp_pos(cb), p.is_float));
                 if (ta) {
                     ja[comp_pos(ca)] = (uint16_t)o;
                     if (++ia < k) ca = TA[tix(offA + ia)];
@@ -641,18 +728,23 @@ size_t sortlist_smem_bytes(int warps)
 cudaError_t sortlist_setup()
 {
     const int bytes = (int)sortlist_smem_bytes(kSortListWarps);
-    cudaError_t e = cudaFuncSetAttribute(sortlist_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(sortlist_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sortlist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    e = cudaFuncSetAttribute(sortlist_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sortlist_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-cudaError_t launch_sortlist(const SegTable& tab, int64_t items, int warps, bool adaptive,
+cudaError_t launch_sortlist(const SegTable& tab, int64_t items, int warps, bool adaptive, bool wide,
                             cudaStream_t stream)
 {
-    if (adaptive)
-        sortlist_kernel<true><<<(unsigned)items, 32 * warps, sortlist_smem_bytes(warps), stream>>>(tab);
+    const size_t bytes = sortlist_smem_bytes(warps);
+    if (wide)
+        sortlist_kernel<false, true><<<(unsigned)items, 32 * warps, bytes, stream>>>(tab);
+    else if (adaptive)
+        sortlist_kernel<true, false><<<(unsigned)items, 32 * warps, bytes, stream>>>(tab);
     else
-        sortlist_kernel<false><<<(unsigned)items, 32 * warps, sortlist_smem_bytes(warps), stream>>>(tab);
+        sortlist_kernel<false, false><<<(unsigned)items, 32 * warps, bytes, stream>>>(tab);
     return cudaGetLastError();
 }
 

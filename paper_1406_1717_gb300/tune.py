@@ -33,7 +33,7 @@ from . import (make_segments, mf_filter, mf_filter_batched, mf_kernel_times, mf_
 
 CLASS_K = (63, 255, 1001, 2047, 4093)          # one representative k per class
 CLASS_MAX = (64, 256, 1021, 2047, 4093, 1 << 30)   # largest k of each class
-FUSED_MAX_K = 1021                             # merge-sort tiles serve 4-byte k up to this
+FUSED_MAX_K = 1021                             # merge-sort tiles serve k up to this
 VARIANTS = (1, 2, 3)                           # merge-sort tiles, warp radix sort, adaptive tiles
 TIER_K = (2047, 3001, 4095, 5001, 6001, 7001, 8001, 9343)
 PIPELINE_ONLY = 1 << 30                        # threshold capped to the pipeline's limit
@@ -185,7 +185,8 @@ def tune_batched(h, x, segs, reps=3) -> dict:
             torch.cuda.synchronize(x.device)
             return e0.elapsed_time(e1) / reps
 
-        variants = VARIANTS if kmax <= FUSED_MAX_K and x.element_size() == 4 else (0,)
+        # the ordered-tile test (variant 3) serves 4-byte elements only
+        variants = (VARIANTS if x.element_size() == 4 else (1, 2)) if kmax <= FUSED_MAX_K else (0,)
         result[str(kmax)] = {"signals": int(sel.size), **_tune_class(h, kmax, groups, total, variants)}
     return result
 

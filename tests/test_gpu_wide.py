@@ -128,3 +128,32 @@ def test_wide_refused_by_32_bit_entry_points():
     y = torch.zeros(1000, dtype=torch.float64, device=DEV)
     assert lib.mf_filter_noalloc(3, x.data_ptr(), 1000, 11, y.data_ptr(), None, None) == 5
     assert lib.mf_fill_splitmix(2, x.data_ptr(), 1000, 1, None) == 5
+
+
+def hi_tie_signals(n, seed):
+    """64-bit keys whose high 32 bits collide often, so that the order rests
+    on the low halves: int64 (a few high words, small low words, negatives)
+    and float64 near 1.0 and -2.0 (equal high words, a few ulps apart)."""
+    rng = np.random.default_rng(seed)
+    i = (rng.integers(-2, 3, size=n).astype(np.int64) << 32) + rng.integers(0, 6, size=n)
+    f = np.where(rng.integers(0, 2, size=n) == 0, 1.0, -2.0) * (1.0 + rng.integers(0, 5, size=n) * 2.0 ** -52)
+    f[rng.integers(0, n, size=max(1, n // 97))] = np.nan
+    return {"int64": i, "float64": f}
+
+
+@pytest.mark.parametrize("k", [1, 3, 31, 101, 255, 511, 1001, 1021])
+def test_wide_sort_variants_on_high_half_ties(k):
+    """Merge-sort tiles (two passes over the key halves) and the radix sort
+    give the oracle's result, bit for bit, on keys tied in their high half."""
+    h = mf.mf_create(0, torch.cuda.current_stream(DEV))
+    try:
+        n = max(40 * k, 20_000) + 333
+        for name, x in hi_tie_signals(n, 7 + k).items():
+            ry, ra = oracle.median_filter(x, k)
+            for variant in (1, 2):
+                mf.mf_set_sort_variant(h, k, variant)
+                y, a = run(h, x, k)
+                assert same_bits(y, ry), (name, k, variant)
+                np.testing.assert_array_equal(a, ra, err_msg=f"{name} variant {variant}")
+    finally:
+        mf.mf_destroy(h)
