@@ -169,7 +169,6 @@ __device__ __forceinline__ void tile_sort(uint64_t* T, uint64_t (&v)[32], int la
     }
 }
 
-__device__ __forceinline__ uint32_t comp_key(uint64_t c) { return (uint32_t)(c >> 10); }
 __device__ __forceinline__ uint32_t comp_pos(uint64_t c) { return (uint32_t)c & 1023u; }
 
 __device__ __forceinline__ uint32_t udiv(uint32_t x, uint64_t magic)
@@ -212,28 +211,101 @@ __device__ __noinline__ int tile_order(const uint32_t* tk, int tile_n, int k, ui
     return asc ? 1 : (desc ? 2 : 0);
 }
 
+// Composite layouts.  4-byte elements: block : 32-bit key : position (22, 32
+// and 10 bits).  8-byte elements: block : top 44 bits of the 64-bit key :
+// position (10, 44, 10); the key's low 20 bits decide only between elements
+// whose top 44 bits are equal.
+template <bool WIDE> struct Comp {
+    static constexpr int kBlk = WIDE ? 54 : 42;         // shift of the block field
+    __device__ __forceinline__ static uint64_t key(uint64_t c)
+    {
+        return (c >> 10) & ((1ull << (kBlk - 10)) - 1ull);
+    }
+    __device__ __forceinline__ static int blk(uint64_t c) { return (int)(c >> kBlk); }
+};
+
 // Key comparison of the pair merges: is A's element (composite ca, CTA
 // element ea) at or before B's (cb, eb) in the window order (A first on equal
-// keys)?  4-byte keys are whole in the composites; 8-byte keys carry their
-// high half there, and equal high halves are decided by the low halves read
-// from x.
+// keys)?  Equal key fields of 8-byte elements are decided by the low halves
+// of the keys, read from x.
 template <bool WIDE>
 __device__ __forceinline__ bool a_first(uint64_t ca, uint64_t cb, const void* x, int64_t ea,
                                         int64_t eb, bool is_float)
 {
-    const uint32_t ka = comp_key(ca), kb = comp_key(cb);
-    if (!WIDE || ka != kb) return ka <= kb;
+    if constexpr (!WIDE) {
+        return (uint32_t)(ca >> 10) <= (uint32_t)(cb >> 10);
+    }
+    const uint64_t ka = Comp<WIDE>::key(ca), kb = Comp<WIDE>::key(cb);
+    if (ka != kb) return ka < kb;
     const uint64_t* x64 = reinterpret_cast<const uint64_t*>(x);
     return (uint32_t)to_key(__ldg(x64 + ea), is_float) <= (uint32_t)to_key(__ldg(x64 + eb), is_float);
 }
 
+// 8-byte elements whose tile has two elements of one block with equal top 44
+// key bits: sort the tile again, least significant digit first (stable LSD on
+// the low 32 and the top 44 bits): by (block, low 32 bits, position), then by
+// (block, top 44 bits, rank after that sort), and put the positions back in
+// the low field.  perm1 / r1: the first sort's permutation and its inverse,
+// in 4 KB of shared memory that the caller does not use until later.
+__device__ __noinline__ void tile_resort_wide(uint64_t* T, const uint64_t* xt, bool is_float, int tile_n,
+                                              int k, uint64_t kmagic, uint16_t* perm1, int lane)
+{
+    using C = Comp<true>;
+    uint16_t* r1 = perm1 + 1024;
+    uint64_t v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int et = 32 * lane + ((i + lane) & 31);
+        uint64_t c = kPadComp;
+        if (et < tile_n) {
+            const uint32_t blk = udiv((uint32_t)et, kmagic);
+            const uint32_t lo = (uint32_t)to_key(__ldg(xt + et), is_float);
+            c = ((uint64_t)blk << C::kBlk) | ((uint64_t)lo << 10) | ((uint32_t)et - blk * (uint32_t)k);
+        }
+        v[i] = c;
+    }
+    __syncwarp();                                       // the caller's reads of T are done
+    tile_sort(T, v, lane);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int t = lane + 32 * i;
+        const uint64_t c = T[tix(t)];
+        if (t < tile_n) {
+            const int e = C::blk(c) * k + (int)(c & 1023u);
+            perm1[t] = (uint16_t)e;
+            r1[e] = (uint16_t)t;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int et = 32 * lane + ((i + lane) & 31);
+        uint64_t c = kPadComp;
+        if (et < tile_n) {
+            const uint32_t blk = udiv((uint32_t)et, kmagic);
+            const uint64_t top = to_key(__ldg(xt + et), is_float) >> 20;
+            c = ((uint64_t)blk << C::kBlk) | (top << 10) | r1[et];
+        }
+        v[i] = c;
+    }
+    __syncwarp();
+    tile_sort(T, v, lane);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int x = lane + 32 * i;
+        const uint64_t c = T[tix(x)];
+        if (x < tile_n) {
+            const int e = perm1[c & 1023u];
+            T[tix(x)] = (c & ~1023ull) | (uint64_t)(e - C::blk(c) * k);
+        }
+    }
+    __syncwarp();
+}
+
 // ADAPTIVE: test every tile for ordered blocks first (sort variant 3).
-// WIDE: 8-byte elements (int64, float64).  The 64-bit order key does not fit
-// a composite, so the tile is sorted twice, least significant half first (a
-// stable LSD sort on two 32-bit digits): by (block, low half, position), then
-// by (block, high half, rank after the first sort).  The first sort's
-// permutation and its inverse stay in the warp's 4 KB of joint-rank space,
-// which the pair merges only use later.
+// WIDE: 8-byte elements (int64, float64), sorted on the top 44 bits of their
+// key; a tile with ties in those bits within a block is sorted again on the
+// whole key (tile_resort_wide).
 template <bool ADAPTIVE, bool WIDE>
 __global__ void __launch_bounds__(kSortListWarps * 32, 2)
 sortlist_kernel(SegTable tab)
@@ -295,6 +367,7 @@ sortlist_kernel(SegTable tab)
     }
     __syncthreads();
     const int order = (ADAPTIVE && !WIDE) ? tile_order(keys + tile_e0, tile_n, k, p.kmagic, lane) : 0;
+    using C = Comp<WIDE>;
     uint64_t v[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
@@ -303,8 +376,8 @@ sortlist_kernel(SegTable tab)
         if (et < tile_n) {
             const uint32_t blk = udiv((uint32_t)et, p.kmagic);
             const uint32_t pos = (uint32_t)et - blk * (uint32_t)k;
-            const uint32_t key = WIDE ? (uint32_t)keys64[tile_e0 + et] : keys[tile_e0 + et];
-            c = ((uint64_t)blk << 42) | ((uint64_t)key << 10) | pos;
+            const uint64_t key = WIDE ? keys64[tile_e0 + et] >> 20 : (uint64_t)keys[tile_e0 + et];
+            c = ((uint64_t)blk << C::kBlk) | (key << 10) | pos;
         }
         v[i] = c;
     }
@@ -319,7 +392,7 @@ sortlist_kernel(SegTable tab)
             const int et = 32 * lane + ((i + lane) & 31);
             int dst = et;
             if (order == 2 && et < tile_n) {
-                const int blk = (int)(v[i] >> 42), pos = (int)(v[i] & 1023u);
+                const int blk = C::blk(v[i]), pos = (int)(v[i] & 1023u);
                 dst = blk * k + min(k, tile_n - blk * k) - 1 - pos;
             }
             T[tix(dst)] = v[i];
@@ -329,47 +402,23 @@ sortlist_kernel(SegTable tab)
         tile_sort(T, v, lane);
     }
     if (WIDE && tile_n > 0) {
-        // second digit: perm1[t] = tile element at rank t after the first
-        // sort, r1[e] = its inverse (16-bit, in this warp's 4 KB after the tiles)
-        uint16_t* perm1 = reinterpret_cast<uint16_t*>(smem + (size_t)W * kTileBytes) + (size_t)warp * 2048;
-        uint16_t* r1 = perm1 + 1024;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int t = lane + 32 * i;
-            const uint64_t c = T[tix(t)];
+        // equal block and top 44 bits in adjacent sorted slots: sort again
+        bool tie = false;
+        uint64_t prev = T[tix(32 * lane)] >> 10;
+#pragma unroll 4
+        for (int i = 1; i <= 32; ++i) {
+            const int t = 32 * lane + i;
             if (t < tile_n) {
-                const int e = (int)(c >> 42) * k + (int)(c & 1023u);
-                perm1[t] = (uint16_t)e;
-                r1[e] = (uint16_t)t;
+                const uint64_t cur = T[tix(t)] >> 10;
+                tie = tie || cur == prev;
+                prev = cur;
             }
         }
-        __syncwarp();
-        // composites (block : high half : r1), the high halves read again from x
-        const uint64_t* xt = reinterpret_cast<const uint64_t*>(p.x) + ebase + tile_e0;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int et = 32 * lane + ((i + lane) & 31);
-            uint64_t c = kPadComp;
-            if (et < tile_n) {
-                const uint32_t blk = udiv((uint32_t)et, p.kmagic);
-                const uint32_t hi = (uint32_t)(to_key(__ldg(xt + et), p.is_float) >> 32);
-                c = ((uint64_t)blk << 42) | ((uint64_t)hi << 10) | r1[et];
-            }
-            v[i] = c;
-        }
-        __syncwarp();
-        tile_sort(T, v, lane);
-        // the low field back from first-sort rank to position in the block
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int x = lane + 32 * i;
-            const uint64_t c = T[tix(x)];
-            if (x < tile_n) {
-                const int e = perm1[c & 1023u];
-                T[tix(x)] = (c & ~1023ull) | (uint64_t)(e - (int)(c >> 42) * k);
-            }
-        }
-        __syncwarp();
+        if (__any_sync(kFull, tie))
+            tile_resort_wide(T, reinterpret_cast<const uint64_t*>(p.x) + ebase + tile_e0, p.is_float,
+                             tile_n, k, p.kmagic,
+                             reinterpret_cast<uint16_t*>(smem + (size_t)W * kTileBytes) + (size_t)warp * 2048,
+                             lane);
     }
     __syncthreads();
 
@@ -434,7 +483,7 @@ sortlist_kernel(SegTable tab)
         const int x = lane + 32 * i;
         if (x < tile_n) {
             const uint32_t pos = comp_pos(v[i]);
-            const uint32_t blk = (uint32_t)(v[i] >> 42);
+            const uint32_t blk = (uint32_t)C::blk(v[i]);
             permW[x] = (uint16_t)pos;
             rnkW[rix(blk * k + pos)] = (uint16_t)(x - blk * k);
         }
