@@ -943,12 +943,14 @@ epilogue_kernel(SegTable tab)
     const int64_t rem = p.n - ebase;
     const int E = (int)((int64_t)(npair + 1) * k < rem ? (int64_t)(npair + 1) * k : rem);
     const ValT* xp = reinterpret_cast<const ValT*>(p.x);
-    if (sizeof(ValT) == 4) {
-        // the span's 16-byte-aligned interior as uint4, the ragged ends one by one
+    {
+        // the span as 32-bit words: its 16-byte-aligned interior as uint4, the
+        // ragged ends one by one
+        const int Ew = E * (int)(sizeof(ValT) / 4);
         const uint32_t* xs4 = reinterpret_cast<const uint32_t*>(xp + ebase);
         uint32_t* xd = reinterpret_cast<uint32_t*>(xs);
-        const int head = min(E, (int)(((16u - ((uint32_t)(uintptr_t)xs4 & 15u)) & 15u) >> 2));
-        const int nvec = (E - head) >> 2;
+        const int head = min(Ew, (int)(((16u - ((uint32_t)(uintptr_t)xs4 & 15u)) & 15u) >> 2));
+        const int nvec = (Ew - head) >> 2;
         const int tail0 = head + 4 * nvec;
         const uint4* xv = reinterpret_cast<const uint4*>(xs4 + head);
         for (int c0 = threadIdx.x; c0 < nvec; c0 += 4 * blockDim.x) {
@@ -968,9 +970,7 @@ epilogue_kernel(SegTable tab)
             }
         }
         if ((int)threadIdx.x < head) xd[threadIdx.x] = __ldg(xs4 + threadIdx.x);
-        if ((int)threadIdx.x < E - tail0) xd[tail0 + threadIdx.x] = __ldg(xs4 + tail0 + threadIdx.x);
-    } else {
-        for (int e = threadIdx.x; e < E; e += blockDim.x) xs[e] = __ldg(xp + ebase + e);
+        if ((int)threadIdx.x < Ew - tail0) xd[tail0 + threadIdx.x] = __ldg(xs4 + tail0 + threadIdx.x);
     }
     __syncthreads();
     const int nout = npair > 0 ? E - k : 0;
