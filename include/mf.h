@@ -223,6 +223,26 @@ mf_status mf_sync(mf_handle h);
 /* Number of kernels this handle has launched since creation (for accounting). */
 mf_status mf_launch_count(mf_handle h, uint64_t* count);
 
+/* Debug build only (libmf_debug.so, compiled with -DMF_DEBUG; the Python
+ * binding loads it when the environment sets MF_DEBUG=1).  Its kernels check
+ * their indices and the invariants of the block data structures (Section 5:
+ * link fields name a slot or a sentinel, 0 <= s <= h, m a live node of its
+ * list whose cached word is current; Section 6.3: s_A + s_B = h after every
+ * step of the large-k tier; a printed node is an element, not a sentinel).
+ * A failed check does not fault: it is counted, the first one's site and
+ * value are kept, and the kernel continues with the index clamped into
+ * range.  mf_debug_take waits for all work on the handle's device, then
+ * returns and clears the records of every kernel file: *count failed checks
+ * in all, *site / *value of the first (sites 1xx fused sort kernel, 2xx chain
+ * and store kernels, 3xx large-k tier, 999 the self-test).  The records are
+ * per process and device, not per handle.  mf_debug_selftest enqueues one
+ * thread that fails one check (site 999, value 42) on the handle's stream,
+ * so a test can see the record reach the host.  Errors: MF_ERR_NULL,
+ * MF_ERR_CUDA; in the normal build both return MF_ERR_UNSUPPORTED (and
+ * mf_debug_take zeroes its outputs). */
+mf_status mf_debug_take(mf_handle h, uint32_t* count, uint32_t* site, uint64_t* value);
+mf_status mf_debug_selftest(mf_handle h);
+
 /* Launch-plan tuning for the window-size class that contains k (classes
  * k <= 64, <= 256, <= 1021, <= 2047, <= 4093, larger): block pairs per CTA
  * of the sort+merge kernel and of the store kernel (0 = built-in choice;

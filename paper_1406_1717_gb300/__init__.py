@@ -11,7 +11,9 @@ fallback: if the library is missing, every call raises.
 Functions carry the C names: ``mf_create``, ``mf_set_stream``, ``mf_filter``,
 ``mf_filter_host``, ``mf_filter_batched``, ``mf_filter_backward``,
 ``mf_filter_noalloc``, ``mf_sync``, ``mf_launch_count``, ``mf_set_tuning``, ``mf_set_timing``,
-``mf_kernel_times``, ``mf_status_str``, ``mf_destroy``.
+``mf_kernel_times``, ``mf_debug_take``, ``mf_debug_selftest``, ``mf_status_str``, ``mf_destroy``.
+With MF_DEBUG=1 in the environment the debug build ``libmf_debug.so`` is
+loaded instead (device checks of indices and list invariants).
 ``median_filter`` is a convenience wrapper that allocates the outputs.
 """
 from __future__ import annotations
@@ -23,7 +25,10 @@ import threading
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libmf.so")
+# MF_DEBUG=1 selects the debug build (device checks; mf_debug_take), made by
+# paper_1406_1717_gb300.build.build(debug=True)
+DEBUG = os.environ.get("MF_DEBUG", "") not in ("", "0")
+LIB_PATH = os.path.join(_PKG, "libmf_debug.so" if DEBUG else "libmf.so")
 
 MF_INT32, MF_FLOAT32, MF_INT64, MF_FLOAT64 = 0, 1, 2, 3
 
@@ -56,8 +61,9 @@ def load_library(path: str = LIB_PATH):
         if _lib is not None:
             return _lib
         if not os.path.exists(path):
-            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
-                               "or python -m paper_1406_1717_gb300.build")
+            how = ("paper_1406_1717_gb300.build.build(debug=True)" if path.endswith("_debug.so")
+                   else "__graft_entry__.build() or python -m paper_1406_1717_gb300.build")
+            raise RuntimeError(f"{path} is missing: build it with {how}")
         lib = ctypes.CDLL(path)
         c = ctypes
         vp, i32, i64, sz = c.c_void_p, c.c_int32, c.c_int64, c.c_size_t
@@ -73,6 +79,9 @@ def load_library(path: str = LIB_PATH):
             "mf_filter_noalloc": ([c.c_int, vp, i64, i32, vp, vp, vp], c.c_int),
             "mf_sync": ([vp], c.c_int),
             "mf_launch_count": ([vp, c.POINTER(c.c_uint64)], c.c_int),
+            "mf_debug_take": ([vp, c.POINTER(c.c_uint32), c.POINTER(c.c_uint32),
+                               c.POINTER(c.c_uint64)], c.c_int),
+            "mf_debug_selftest": ([vp], c.c_int),
             "mf_set_timing": ([vp, c.c_int], c.c_int),
             "mf_set_tuning": ([vp, i32, i32, i32], c.c_int),
             "mf_set_sort_variant": ([vp, i32, i32], c.c_int),
@@ -229,6 +238,21 @@ def mf_launch_count(handle) -> int:
     c = ctypes.c_uint64()
     _check(load_library().mf_launch_count(handle, ctypes.byref(c)), "mf_launch_count")
     return int(c.value)
+
+
+def mf_debug_take(handle):
+    """Debug build: (failed checks, first site, first value) since the last
+    take, after all work on the device finished; the records are cleared.
+    Raises MFError(MF_ERR_UNSUPPORTED) in the normal build."""
+    cnt, site, val = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+    _check(load_library().mf_debug_take(handle, ctypes.byref(cnt), ctypes.byref(site),
+                                        ctypes.byref(val)), "mf_debug_take")
+    return int(cnt.value), int(site.value), int(val.value)
+
+
+def mf_debug_selftest(handle):
+    """Debug build: one device thread fails one check (site 999, value 42)."""
+    _check(load_library().mf_debug_selftest(handle), "mf_debug_selftest")
 
 
 KERNEL_NAMES = ("sort", "unwind", "chain", "store")

@@ -457,6 +457,44 @@ mf_status mf_sync(mf_handle h) {
     return cuda_status(cudaStreamSynchronize(h->stream));
 }
 
+mf_status mf_debug_take(mf_handle h, uint32_t* count, uint32_t* site, uint64_t* value) {
+    if (!h || !count || !site || !value) return MF_ERR_NULL;
+    *count = 0;
+    *site = 0;
+    *value = 0;
+#ifdef MF_DEBUG
+    DeviceGuard g(h->device);
+    if (!g.ok) return MF_ERR_CUDA;
+    cudaError_t e = cudaDeviceSynchronize();          // kernels of every stream, aux included
+    using Take = cudaError_t (*)(uint32_t*, uint32_t*, uint64_t*);
+    const Take takes[] = {mf::debug_take_sortlist, mf::debug_take_pipeline, mf::debug_take_large};
+    for (Take t : takes) {
+        uint32_t c = 0, st = 0;
+        uint64_t v = 0;
+        if (e == cudaSuccess) e = t(&c, &st, &v);
+        if (c > 0 && *count == 0) {
+            *site = st;
+            *value = v;
+        }
+        *count += c;
+    }
+    return cuda_status(e);
+#else
+    return MF_ERR_UNSUPPORTED;
+#endif
+}
+
+mf_status mf_debug_selftest(mf_handle h) {
+    if (!h) return MF_ERR_NULL;
+#ifdef MF_DEBUG
+    DeviceGuard g(h->device);
+    if (!g.ok) return MF_ERR_CUDA;
+    return cuda_status(mf::debug_selftest(h->stream));
+#else
+    return MF_ERR_UNSUPPORTED;
+#endif
+}
+
 mf_status mf_launch_count(mf_handle h, uint64_t* count) {
     if (!h || !count) return MF_ERR_NULL;
     *count = h->stats.launches;

@@ -18,6 +18,52 @@ namespace mf {
 constexpr uint32_t kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
+// Debug build (compiled with -DMF_DEBUG): the kernels check their indices and
+// the block data structures' invariants (Section 5: link fields name a slot
+// or a sentinel, 0 <= s <= h, m is a live node of its list).  A failed check
+// counts itself, keeps the first site and value in this translation unit's
+// record, and the kernel carries on with the index clamped into range, so no
+// check faults, traps or waits.  mf_debug_take (mf_api.cu) reads and clears
+// the records of all translation units.  In the normal build MF_CHECK is the
+// constant true and its arguments are not evaluated.
+// Sites: 1xx fused sort kernel, 2xx chain and store kernels, 3xx large-k
+// tier, 999 the self-test.
+// ---------------------------------------------------------------------------
+#ifdef MF_DEBUG
+namespace {
+__device__ unsigned int g_dbg_count;
+__device__ unsigned int g_dbg_site;
+__device__ unsigned long long g_dbg_value;
+__device__ __noinline__ bool debug_check(bool ok, uint32_t site, uint64_t value)
+{
+    if (!ok && atomicAdd(&g_dbg_count, 1u) == 0u) {
+        g_dbg_site = site;
+        g_dbg_value = value;
+    }
+    return ok;
+}
+}  // namespace
+#define MF_CHECK(cond, site, value) ::mf::debug_check((cond), (site), (uint64_t)(value))
+// Host side of this translation unit's record: read it, then clear it.
+#define MF_DEBUG_TAKE_FN(name)                                                              \
+    cudaError_t debug_take_##name(uint32_t* count, uint32_t* site, uint64_t* value)         \
+    {                                                                                       \
+        cudaError_t e = cudaMemcpyFromSymbol(count, g_dbg_count, sizeof(uint32_t));         \
+        if (e == cudaSuccess) e = cudaMemcpyFromSymbol(site, g_dbg_site, sizeof(uint32_t)); \
+        if (e == cudaSuccess) e = cudaMemcpyFromSymbol(value, g_dbg_value, sizeof(uint64_t)); \
+        const uint32_t z32 = 0u;                                                            \
+        const uint64_t z64 = 0ull;                                                          \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_dbg_count, &z32, sizeof(uint32_t));  \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_dbg_site, &z32, sizeof(uint32_t));   \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_dbg_value, &z64, sizeof(uint64_t));  \
+        return e;                                                                           \
+    }
+#else
+#define MF_CHECK(cond, site, value) true
+#define MF_DEBUG_TAKE_FN(name)
+#endif
+
+// ---------------------------------------------------------------------------
 // Order keys.  int32: flipping the sign bit turns signed order into unsigned
 // order.  float32: IEEE 754 totalOrder on bit patterns becomes unsigned order
 // after flipping all bits of negatives and the sign bit of non-negatives.

@@ -152,4 +152,14 @@ cudaError_t backward_setup();
 cudaError_t launch_backward(const float* gy, const int32_t* argmed, int64_t rows, int64_t n, int k,
                             float* gx, cudaStream_t stream, uint64_t* launches);
 
+#ifdef MF_DEBUG
+// Debug build: each translation unit's record of failed device checks (read
+// and cleared), and a one-thread kernel that fails one check on purpose
+// (site 999, value 42) so that the recording itself can be tested.
+cudaError_t debug_take_sortlist(uint32_t* count, uint32_t* site, uint64_t* value);
+cudaError_t debug_take_pipeline(uint32_t* count, uint32_t* site, uint64_t* value);
+cudaError_t debug_take_large(uint32_t* count, uint32_t* site, uint64_t* value);
+cudaError_t debug_selftest(cudaStream_t stream);
+#endif
+
 }  // namespace mf

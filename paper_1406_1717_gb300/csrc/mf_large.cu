@@ -607,21 +607,31 @@ large_chain(LargeTable tab, int64_t items)
     uint32_t mA = (uint32_t)st.x, mB = (uint32_t)st.y;
     int sA = st.z, sB = st.w;
     for (int t = i0; t < min(i0 + kAhead, i1); ++t) prefetch_l2(Lq + __ldg(JA + t));
+#ifdef MF_DEBUG
+    const uint32_t nmax = 2u * (uint32_t)p.k + 1u;          // sentinel B, the largest node
+    auto node = [&](uint32_t r, uint32_t site) { return MF_CHECK(r <= nmax, site, r) ? r : nmax; };
+#else
+    auto node = [](uint32_t r, uint32_t) { return r; };
+#endif
+    mA = node(mA, 301);
+    mB = node(mB, 301);
     for (int i = i0; i < i1; ++i) {
-        const uint32_t a = __ldg(JA + i), b = __ldg(JB + i);
-        const uint2 u = __ldg(UL + i);
+        const uint32_t a = node(__ldg(JA + i), 301), b = node(__ldg(JB + i), 301);
+        uint2 u = __ldg(UL + i);
+        u.x = node(u.x, 301);
+        u.y = node(u.y, 301);
         if (i + kAhead < i1) prefetch_l2(Lq + __ldg(JA + i + kAhead));
         const uint2 La = Lq[a];
         const uint2 LmA = Lq[mA];
         const uint2 LmB = Lq[mB];
         // delete(A, i): unlink node a, then keep s_A and m consistent
-        const uint32_t na = La.x, pa = La.y;
+        const uint32_t na = node(La.x, 301), pa = node(La.y, 301);
         NXp[2 * pa] = na;
         NXp[2 * na + 1] = pa;
         if (a < mA) {
             --sA;
         } else {
-            uint32_t pvm = (mA == na) ? pa : LmA.y;        // prev of m after the unlink
+            uint32_t pvm = (mA == na) ? pa : node(LmA.y, 301);   // prev of m after the unlink
             if (mA == a) { mA = na; pvm = pa; }
             if (sA > 0) { mA = pvm; --sA; }
         }
@@ -629,12 +639,15 @@ large_chain(LargeTable tab, int64_t items)
         Lq[b] = make_uint2(u.y, u.x);
         NXp[2 * u.x] = b;
         NXp[2 * u.y + 1] = b;
-        if (b < mB) mB = (mB == u.y) ? b : LmB.y;
+        if (b < mB) mB = (mB == u.y) ? b : node(LmB.y, 301);
         // advance the smaller peek while s_A + s_B < h
         if (sA + sB < h) {
-            if (mA < mB) { mA = Lq[mA].x; ++sA; }
-            else         { mB = Lq[mB].x; ++sB; }
+            if (mA < mB) { mA = node(Lq[mA].x, 301); ++sA; }
+            else         { mB = node(Lq[mB].x, 301); ++sB; }
         }
+        // Section 6.3: s_A + s_B = h after every step; the median is an element
+        (void)MF_CHECK(sA >= 0 && sB >= 0 && sA + sB == h, 302, (uint64_t)(uint32_t)sA << 32 | (uint32_t)sB);
+        (void)MF_CHECK((mA < mB ? mA : mB) < 2u * (uint32_t)p.k, 303, mA < mB ? mA : mB);
         OUT[i] = mA < mB ? mA : mB;                        // joint rank of the median
     }
 }
@@ -657,6 +670,7 @@ large_epilogue(LargeTable tab, int64_t items)
         const uint32_t id = __ldg(p.M + q * 2 * p.kp + r);
         src = (q + (id >> 31)) * (int64_t)p.k + (id & ~kBFlag);
     }
+    if (!MF_CHECK(src >= 0 && src < p.n, 304, src)) src = 0;
     reinterpret_cast<ValT*>(p.y)[o] = __ldg(reinterpret_cast<const ValT*>(p.x) + src);
     if (p.argmed) p.argmed[o] = (int32_t)src;
 }
@@ -901,5 +915,7 @@ cudaError_t launch_large_batched(const void* x, void* y, int32_t* argmed, Elem e
     if (el.wide) return run_large<uint64_t>(tab, tot, ntier, kmax, stream, stats);
     return run_large<uint32_t>(tab, tot, ntier, kmax, stream, stats);
 }
+
+MF_DEBUG_TAKE_FN(large)
 
 }  // namespace mf

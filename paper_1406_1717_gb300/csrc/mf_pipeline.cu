@@ -384,7 +384,13 @@ struct Lists {
     uint16_t* jr16;           // wide format: this lane's rank array
     uint8_t* jr8;             // mid format: this lane's array of rank bits 4..0
     uint32_t NL;              // lanes of this warp: slot e's word is w[e * NL]
+    uint32_t lim, h;          // k + 1 (sentinel B, the largest slot) and h: debug checks only
     __device__ __forceinline__ uint32_t ld(uint32_t e) const { return w[e * NL]; }
+    // x as a slot; the debug build clamps a value that is not one into range
+    __device__ __forceinline__ uint32_t cl(uint32_t x, uint32_t site) const
+    {
+        return MF_CHECK(x <= lim, site, x) ? x : lim;
+    }
     __device__ __forceinline__ void st(uint32_t e, uint32_t v) const { w[e * NL] = v; }
     __device__ __forceinline__ void xr(uint32_t e, uint32_t v) const { atomicXor(&w[e * NL], v); }
     // relinks: next(e) <- v (old value `old`), prev(e) <- v
@@ -448,19 +454,19 @@ __device__ __forceinline__ uint32_t pair_step_packed(PairState& st, const Lists<
                                                      uint32_t* wnext)
 {
     using LL = Lists<kFmtPacked>;
-    const uint32_t pm = LL::prv(st.wmA), nm = LL::nxt(st.wmA);
-    const uint32_t pmB = LL::prv(st.wmB), nmB = LL::nxt(st.wmB);
+    const uint32_t pm = L.cl(LL::prv(st.wmA), 201), nm = L.cl(LL::nxt(st.wmA), 201);
+    const uint32_t pmB = L.cl(LL::prv(st.wmB), 201), nmB = L.cl(LL::nxt(st.wmB), 201);
     // -------- relinks: delete(A, i), undelete(B, i) --------------------------------
-    const uint32_t pa = LL::prv(wa), na = LL::nxt(wa), ra = wa >> 20;
-    const uint32_t pb = LL::prv(wbw), nb = LL::nxt(wbw), rb = wbw >> 20;
+    const uint32_t pa = L.cl(LL::prv(wa), 201), na = L.cl(LL::nxt(wa), 201), ra = wa >> 20;
+    const uint32_t pb = L.cl(LL::prv(wbw), 201), nb = L.cl(LL::nxt(wbw), 201), rb = wbw >> 20;
     L.xr(pa, na ^ i);                                   // next[prev[i]] <- next[i]
     L.xr(na, (pa ^ i) << 10);                           // prev[next[i]] <- prev[i]
     L.st(i, wbw);
     L.xr(pb, nb ^ i);                                   // next[prev[i]] <- i
     L.xr(nb, (pb ^ i) << 10);                           // prev[next[i]] <- i
     // -------- the candidates' words, after the relinks ------------------------
-    const uint32_t wmA = L.ld(st.mA), wpm = L.ld(pm), wnm = L.ld(nm);
-    const uint32_t wmB = L.ld(st.mB), wpmB = L.ld(pmB), wnmB = L.ld(nmB);
+    const uint32_t wmA = L.ld(L.cl(st.mA, 202)), wpm = L.ld(pm), wnm = L.ld(nm);
+    const uint32_t wmB = L.ld(L.cl(st.mB, 202)), wpmB = L.ld(pmB), wnmB = L.ld(nmB);
     *wnext = L.ld(i + 1);
     // -------- delete(A, i): the m pointer and s -----------------------------------
     const bool small = ra < st.rmA;                     // alpha[i] small (or m at the end)
@@ -506,10 +512,12 @@ __device__ __forceinline__ uint32_t pair_step_after(PairState& st, const Lists<F
                                                     uint32_t rb, uint32_t* wnext, uint32_t* rnext)
 {
     using LL = Lists<FMT>;
-    const uint32_t pm = LL::prv(st.wmA), nm = LL::nxt(st.wmA);
-    const uint32_t pmB = LL::prv(st.wmB), nmB = LL::nxt(st.wmB);
+    const uint32_t pm = L.cl(LL::prv(st.wmA), 201), nm = L.cl(LL::nxt(st.wmA), 201);
+    const uint32_t pmB = L.cl(LL::prv(st.wmB), 201), nmB = L.cl(LL::nxt(st.wmB), 201);
+    pb = L.cl(pb, 201);
+    nb = L.cl(nb, 201);
     // -------- relinks: delete(A, i), undelete(B, i) --------------------------------
-    const uint32_t pa = LL::prv(wa), na = LL::nxt(wa);
+    const uint32_t pa = L.cl(LL::prv(wa), 201), na = L.cl(LL::nxt(wa), 201);
     const uint32_t wbw = LL::make(pb, nb, rb);
     L.set_next(pa, na, i);                              // next[prev[i]] <- next[i]
     L.set_prev(na, pa, i);                              // prev[next[i]] <- prev[i]
@@ -518,8 +526,8 @@ __device__ __forceinline__ uint32_t pair_step_after(PairState& st, const Lists<F
     L.set_next(pb, i, nb);                              // next[prev[i]] <- i
     L.set_prev(nb, i, pb);                              // prev[next[i]] <- i
     // -------- the candidates' words and ranks, after the relinks -----------------
-    const uint32_t wmA = L.ld(st.mA), wpm = L.ld(pm), wnm = L.ld(nm);
-    const uint32_t wmB = L.ld(st.mB), wpmB = L.ld(pmB), wnmB = L.ld(nmB);
+    const uint32_t wmA = L.ld(L.cl(st.mA, 202)), wpm = L.ld(pm), wnm = L.ld(nm);
+    const uint32_t wmB = L.ld(L.cl(st.mB, 202)), wpmB = L.ld(pmB), wnmB = L.ld(nmB);
     const uint32_t wn = L.ld(i + 1);
     const uint32_t rpm = L.rank(pm, wpm), rnm = L.rank(nm, wnm);
     const uint32_t rpmB = L.rank(pmB, wpmB), rnmB = L.rank(nmB, wnmB);
@@ -561,6 +569,24 @@ __device__ __forceinline__ uint32_t pair_step_after(PairState& st, const Lists<F
     return st.rmA < st.rmB ? st.mA : (0x8000u | st.mB);
 }
 
+// Debug build: the state after a step satisfies Section 5's invariants: 0 <=
+// s_A <= h, m_A and m_B are live nodes of their lists (next(prev(m)) = m) whose
+// cached words are current, and the printed node is an element, not a
+// sentinel.
+template <int FMT>
+__device__ __forceinline__ void check_state(const PairState& st, const Lists<FMT>& L, uint32_t out)
+{
+#ifdef MF_DEBUG
+    using LL = Lists<FMT>;
+    (void)MF_CHECK(st.sA >= 0 && (uint32_t)st.sA <= L.h, 203, st.sA);
+    (void)MF_CHECK(L.ld(L.cl(st.mA, 202)) == st.wmA &&
+                   LL::nxt(L.ld(L.cl(LL::prv(st.wmA), 201))) == st.mA, 204, st.mA);
+    (void)MF_CHECK(L.ld(L.cl(st.mB, 202)) == st.wmB &&
+                   LL::nxt(L.ld(L.cl(LL::prv(st.wmB), 201))) == st.mB, 205, st.mB);
+    (void)MF_CHECK((out & 0x7fffu) + 1u < L.lim, 206, out);
+#endif
+}
+
 template <int FMT>
 __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, int lane, int64_t q,
                                            uint32_t rec_words, uint32_t NL, bool copy)
@@ -574,6 +600,8 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
     L.jr16 = reinterpret_cast<uint16_t*>(wsl + rec_words * NL + lane);
     L.jr8 = reinterpret_cast<uint8_t*>(wsl + rec_words * NL + lane);
     L.NL = NL;
+    L.lim = (uint32_t)k + 1u;
+    L.h = (uint32_t)h;
 
     // ---- construct(A) in slot space + empty B (rows of kp elements) ----------
     const size_t abase = (size_t)q * p.kp;              // block j-1 = q
@@ -646,6 +674,7 @@ __device__ __forceinline__ void chain_body(const PipeParams& p, uint32_t* wsl, i
                     o = pair_step_after<FMT>(st, L, (uint32_t)i, wa, ra, pb, nb, rb, &wn, &rn);
                     ra = rn;
                 }
+                check_state(st, L, o);
                 wa = wn;
                 ov[t >> 1] |= (t & 1) ? (o << 16) : o;
             }
@@ -717,6 +746,8 @@ __device__ __forceinline__ void chain_body_words(const PipeParams& p, uint32_t* 
     L.w = wsl + lane;
     L.jr16 = nullptr;
     L.NL = NL;
+    L.lim = (uint32_t)k + 1u;
+    L.h = (uint32_t)h;
     if (copy) {
         // slots 0 .. k+1 by this lane: 16 loads of 16 bytes in flight, then their stores
         const uint4* wa4 = reinterpret_cast<const uint4*>(p.wA + (size_t)q * p.kw);
@@ -768,6 +799,7 @@ __device__ __forceinline__ void chain_body_words(const PipeParams& p, uint32_t* 
                 const uint32_t w = wbv[t];
                 uint32_t wn;
                 const uint32_t o = pair_step_packed(st, L, (uint32_t)i, wa, w, &wn);
+                check_state(st, L, o);
                 wa = wn;
                 ov[t >> 1] |= (t & 1) ? (o << 16) : o;
             }
@@ -995,7 +1027,8 @@ epilogue_kernel(SegTable tab)
                 for (int u = 0; u < 4; ++u) {
                     const int i = i0 + u * stride;
                     if (i < cnt) {
-                        const int e = gk + (int)(id[u] >> 15) * k + (int)(id[u] & 0x7fffu);
+                        int e = gk + (int)(id[u] >> 15) * k + (int)(id[u] & 0x7fffu);
+                        if (!MF_CHECK(e >= 0 && e < E, 207, e)) e = 0;
                         ys[gk + i] = xs[e];
                         if (as) as[gk + i] = (int32_t)(ebase + e);
                     }
@@ -1020,7 +1053,8 @@ epilogue_kernel(SegTable tab)
             for (int u = 0; u < 4; ++u) {
                 const int o = o0 + u * stride;
                 if (o < nout) {
-                    const int e = gk[u] + (int)(id[u] >> 15) * k + (int)(id[u] & 0x7fffu);
+                    int e = gk[u] + (int)(id[u] >> 15) * k + (int)(id[u] & 0x7fffu);
+                    if (!MF_CHECK(e >= 0 && e < E, 207, e)) e = 0;
                     ys[o] = xs[e];
                     if (as) as[o] = (int32_t)(ebase + e);
                 }
@@ -1468,5 +1502,18 @@ cudaError_t launch_pipeline_batched(const void* x, void* y, int32_t* argmed, Ele
     if (e != cudaSuccess) return e;
     return launch_classes(plans, tabs, tot, ncls, stream, stats);
 }
+
+#ifdef MF_DEBUG
+// One thread fails one check on purpose (no memory access depends on it), so
+// that a test can see the record reach the host.
+__global__ void debug_selftest_kernel() { (void)MF_CHECK(false, 999u, 42u); }
+
+cudaError_t debug_selftest(cudaStream_t stream)
+{
+    debug_selftest_kernel<<<1, 1, 0, stream>>>();
+    return cudaGetLastError();
+}
+#endif
+MF_DEBUG_TAKE_FN(pipeline)
 
 }  // namespace mf

@@ -176,6 +176,15 @@ __device__ __forceinline__ uint32_t udiv(uint32_t x, uint64_t magic)
     return (uint32_t)(((uint64_t)x * magic) >> 32);
 }
 
+// Debug build: a list word's link fields name a slot or a sentinel (at most
+// k + 1), its rank field a joint rank (below 2k) or the sentinel rank.
+__device__ __forceinline__ uint32_t checked_word(uint32_t w, int k, uint32_t site)
+{
+    (void)MF_CHECK((w & 1023u) <= (uint32_t)k + 1u && ((w >> 10) & 1023u) <= (uint32_t)k + 1u &&
+                   ((w >> 20) < 2u * (uint32_t)k || (w >> 20) == kRankInf), site, w);
+    return w;
+}
+
 // Adaptive step (Section 1: an adaptive sort gives an adaptive median
 // filter): 1 when every block of the tile is in ascending order (the stable
 // order is then the position order), 2 when every block is strictly
@@ -456,10 +465,10 @@ sortlist_kernel(SegTable tab)
                 const bool ta = ib >= NB ||
                                 (ia < k && a_first<WIDE>(ca, cb, p.x, eA + comp_pos(ca), eB + comp_pos(cb), p.is_float));
                 if (ta) {
-                    ja[comp_pos(ca)] = (uint16_t)o;
+                    if (MF_CHECK(comp_pos(ca) < (uint32_t)k && o < tot, 101, o)) ja[comp_pos(ca)] = (uint16_t)o;
                     if (++ia < k) ca = TA[tix(offA + ia)];
                 } else {
-                    jb[comp_pos(cb)] = (uint16_t)o;
+                    if (MF_CHECK(comp_pos(cb) < (uint32_t)NB && o < tot, 101, o)) jb[comp_pos(cb)] = (uint16_t)o;
                     if (++ib < NB) cb = TB[tix(offB + ib)];
                 }
             }
@@ -485,7 +494,8 @@ sortlist_kernel(SegTable tab)
             const uint32_t pos = comp_pos(v[i]);
             const uint32_t blk = (uint32_t)C::blk(v[i]);
             permW[x] = (uint16_t)pos;
-            rnkW[rix(blk * k + pos)] = (uint16_t)(x - blk * k);
+            if (MF_CHECK(blk * k + pos < (uint32_t)tile_n && x - (int)blk * k < k, 102, x))
+                rnkW[rix(blk * k + pos)] = (uint16_t)(x - blk * k);
         }
     }
     __syncwarp();
@@ -508,11 +518,12 @@ sortlist_kernel(SegTable tab)
                     const int t = rnkW[rix(boff + pos)];
                     const uint32_t pv = t > 0 ? pm[t - 1] : (uint32_t)k;
                     const uint32_t nx = t + 1 < k ? pm[t + 1] : (uint32_t)k;
-                    wa[pos] = nx | (pv << 10) | ((uint32_t)ja[pos] << 20);
+                    wa[pos] = checked_word(nx | (pv << 10) | ((uint32_t)ja[pos] << 20), k, 103);
                 }
                 wa[k] = (uint32_t)pm[0] | ((uint32_t)pm[k - 1] << 10) | (kRankInf << 20);
                 wa[k + 1] = (uint32_t)(k + 1) | ((uint32_t)(k + 1) << 10) | (kRankInf << 20);
                 wa[k + 2] = pm[p.h];
+                (void)MF_CHECK(pm[p.h] < (uint32_t)k, 104, pm[p.h]);
             } else if (npair == 0) {
                 p.wA[k + 2] = pm[p.h];                  // one block only: y[0] = X_0[P_0[h]]
             }
@@ -527,7 +538,7 @@ sortlist_kernel(SegTable tab)
                     const uint64_t above = seen & ~((2ull << r) - 1ull);   // r = 63: 0
                     const uint32_t pv = below ? (uint32_t)pm[63 - __clzll((long long)below)] : sentB;
                     const uint32_t nx = above ? (uint32_t)pm[__ffsll((long long)above) - 1] : sentB;
-                    wb[pos] = nx | (pv << 10) | ((uint32_t)jb[pos] << 20);
+                    wb[pos] = checked_word(nx | (pv << 10) | ((uint32_t)jb[pos] << 20), k, 103);
                     seen |= 1ull << r;
                 }
             }
@@ -552,7 +563,7 @@ sortlist_kernel(SegTable tab)
             const uint32_t pv = t > 0 ? pm[t - 1] : (uint32_t)k;
             const uint32_t nx = t + 1 < k ? pm[t + 1] : (uint32_t)k;
             p.wA[(size_t)(j0 - 1 + b) * p.kw + pos] =
-                nx | (pv << 10) | ((uint32_t)jaS[(size_t)b * k + pos] << 20);
+                checked_word(nx | (pv << 10) | ((uint32_t)jaS[(size_t)b * k + pos] << 20), k, 103);
         }
         for (int bt = lane; bt < nbt; bt += 32) {
             const int b = warp * bpw + bt;
@@ -562,6 +573,7 @@ sortlist_kernel(SegTable tab)
                 wa[k] = (uint32_t)pm[0] | ((uint32_t)pm[k - 1] << 10) | (kRankInf << 20);
                 wa[k + 1] = (uint32_t)(k + 1) | ((uint32_t)(k + 1) << 10) | (kRankInf << 20);
                 wa[k + 2] = pm[p.h];
+                (void)MF_CHECK(pm[p.h] < (uint32_t)k, 104, pm[p.h]);
             } else if (npair == 0) {
                 p.wA[k + 2] = pm[p.h];                  // one block only: y[0] = X_0[P_0[h]]
             }
@@ -639,7 +651,7 @@ sortlist_kernel(SegTable tab)
                 if (bx < 1) continue;
                 const int pos = x - btx * k;
                 p.wB[(size_t)(j0 - 1 + bx - 1) * p.kw + pos] =
-                    areaW[tix(x)] | ((uint32_t)jbS[(size_t)(bx - 1) * k + pos] << 20);
+                    checked_word(areaW[tix(x)] | ((uint32_t)jbS[(size_t)(bx - 1) * k + pos] << 20), k, 103);
             }
             __syncwarp();
         }
@@ -668,13 +680,14 @@ sortlist_kernel(SegTable tab)
                     const int pos = pos0 + 32 * u;
                     const uint32_t pv = t[u] > 0 ? pm[t[u] - 1] : (uint32_t)k;
                     const uint32_t nx = t[u] + 1 < k ? pm[t[u] + 1] : (uint32_t)k;
-                    if (pos < k) wa[pos] = nx | (pv << 10) | (jv[u] << 20);
+                    if (pos < k) wa[pos] = checked_word(nx | (pv << 10) | (jv[u] << 20), k, 103);
                 }
             }
             if (lane == 0) {
                 wa[k] = (uint32_t)pm[0] | ((uint32_t)pm[k - 1] << 10) | (kRankInf << 20);
                 wa[k + 1] = (uint32_t)(k + 1) | ((uint32_t)(k + 1) << 10) | (kRankInf << 20);
                 wa[k + 2] = pm[p.h];
+                (void)MF_CHECK(pm[p.h] < (uint32_t)k, 104, pm[p.h]);
             }
         } else if (npair == 0 && lane == 0) {
             p.wA[k + 2] = pm[p.h];                      // one block only: y[0] = X_0[P_0[h]]
@@ -761,7 +774,7 @@ sortlist_kernel(SegTable tab)
             uint32_t* wb = p.wB + (size_t)(j0 - 1 + b - 1) * p.kw;
             const uint16_t* jb = jbS + (size_t)(b - 1) * k;
             for (int pos = lane; pos < NB; pos += 32)
-                wb[pos] = areaW[tix(pos)] | ((uint32_t)jb[pos] << 20);
+                wb[pos] = checked_word(areaW[tix(pos)] | ((uint32_t)jb[pos] << 20), k, 103);
             __syncwarp();
         }
     }
@@ -796,5 +809,7 @@ cudaError_t launch_sortlist(const SegTable& tab, int64_t items, int warps, bool 
         sortlist_kernel<false, false><<<(unsigned)items, 32 * warps, bytes, stream>>>(tab);
     return cudaGetLastError();
 }
+
+MF_DEBUG_TAKE_FN(sortlist)
 
 }  // namespace mf

@@ -91,3 +91,21 @@ def test_binding_refuses_missing_library(tmp_path):
             mf.load_library(str(tmp_path / "missing.so"))
     finally:
         mf._lib = saved
+
+
+def test_debug_entries_check_their_arguments(lib):
+    vp = ctypes.c_void_p
+    c, s, v = ctypes.c_uint32(7), ctypes.c_uint32(7), ctypes.c_uint64(7)
+    assert lib.mf_debug_take(None, ctypes.byref(c), ctypes.byref(s), ctypes.byref(v)) == 1
+    assert lib.mf_debug_selftest(None) == 1
+
+
+def test_debug_build_compiles_and_exports_the_boundary():
+    """The MF_DEBUG build (device checks that record and clamp) compiles for
+    sm_103a and exports the same functions; it is loaded here without being
+    called (no GPU)."""
+    path = mfbuild.build(debug=True)
+    assert path.endswith("libmf_debug.so") and os.path.exists(path)
+    dbg = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(dbg, name), name
