@@ -20,7 +20,7 @@
 //                     before the run
 //   large_seginit     rebuilds the lists before step i0 of a pair (Section 6.3
 //                     invariant: S_A u S_B are the h smallest of the window)
-//                     from bitsets of the window's joint ranks
+//                     in two coalesced passes over the pair's merged order
 //   large_chain       the steps i0 .. i1-1 of Section 6.2 from that state,
 //                     one thread per (pair, segment), lists in global memory
 //   large_epilogue    node -> input element, y / argmed
@@ -462,114 +462,157 @@ large_unwind(LargeTable tab)
     }
 }
 
-// One CTA per (pair q, segment s), i0 = s * L: the lists before step i0.
-// The window is A's positions >= i0 and B's positions < i0.  KA / KB mark
-// the joint ranks of its A and B elements; a node's list neighbours are the
-// nearest marked ranks of its own block, and the small elements are the
-// window's h smallest (Section 6.3 invariant), found by a prefix count.
+// One CTA per (pair q, segment s): the state before step i0 = s L (Section
+// 6.3: S_A u S_B are the h smallest elements of the window A[i0 .. k) u
+// B[0 .. i0)), from the pair's merged order M in two coalesced passes.  Joint
+// rank r is kept in A's list if it is an element of A at a position >= i0,
+// in B's list if it is an element of B at a position < i0; a kept node's
+// neighbours are the nearest kept ranks of its own list (sentinels SA = 2k,
+// SB = 2k + 1).  Pass 1: every warp counts the kept nodes of its range of
+// ranks (32 per ballot) and notes its first and last.  Pass 2: every kept
+// node writes its prev (the highest kept rank of its list below it in the
+// same 32, else the carry: the last kept rank before those 32) and, as its
+// predecessor's next, itself; the warp whose ranks hold the window's element
+// of rank h records s_A and the last kept rank of each list below it.  Both
+// passes keep eight loads of M in flight per lane.
 __global__ void __launch_bounds__(256)
 large_seginit(LargeTable tab)
 {
-    extern __shared__ __align__(16) uint32_t sw[];
+    constexpr int kW = 8;                          // warps per CTA
+    constexpr int kAhead = 8;                      // chunks of 32 ranks loaded at once
+    constexpr uint32_t kNone = 0xffffffffu;        // past the window: neither list
+    __shared__ int s_cnt[2][kW], s_first[2][kW], s_last[2][kW];
+    __shared__ int s_res[3];                       // s_A, last kept A / B rank below T
     int64_t sid;
     const LargeParams p = find_large(tab, kLSeg, blockIdx.x, &sid);
-    const int nw = (2 * p.k + 31) / 32, ns = (nw + 31) / 32;
     const int64_t q = sid / p.S;
     const int s = (int)(sid - q * p.S);
     const int NB = block_len(p, q + 1);
     const int i0 = s * p.L;
     if (i0 >= NB) return;
     const int k = p.k, h = p.h, tot = k + NB;
-    uint32_t* KA = sw;
-    uint32_t* KB = KA + nw;
-    uint32_t* KA1 = KB + nw;
-    uint32_t* KB1 = KA1 + ns;
-    int* scan = reinterpret_cast<int*>(KB1 + ns); // 2 * blockDim.x
-    int* sh_state = scan + 2 * blockDim.x;        // T, s_A
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t* M = p.M + q * 2 * p.kp;
-    for (int w = warp; w < nw; w += nwarp) {
-        const int r = (w << 5) + lane;
-        const uint32_t id = r < tot ? __ldg(M + r) : 0u;
+    const int nch = (tot + 31) >> 5;
+    const int per = (nch + kW - 1) / kW;
+    const int c0 = min(nch, warp * per), c1 = min(nch, c0 + per);
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t SA = 2u * (uint32_t)k, SB = SA + 1u;
+    uint32_t* NX = reinterpret_cast<uint32_t*>(p.lists + sid * p.LN);   // next of r at [2r], prev at [2r+1]
+    auto load = [&](int cb, uint32_t (&ids)[kAhead]) {
+#pragma unroll
+        for (int j = 0; j < kAhead; ++j) {
+            const int r = ((cb + j) << 5) + lane;
+            ids[j] = cb + j < c1 && r < tot ? __ldg(M + r) : kNone;
+        }
+    };
+    auto kept = [&](uint32_t id, int l) {
         const bool isB = (id & kBFlag) != 0;
-        const uint32_t pos = id & ~kBFlag;
-        const uint32_t a = __ballot_sync(kFull, r < tot && !isB && pos >= (uint32_t)i0);
-        const uint32_t bb = __ballot_sync(kFull, r < tot && isB && pos < (uint32_t)i0);
-        if (lane == 0) { KA[w] = a; KB[w] = bb; }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < ns; t += blockDim.x) {
-        uint32_t sa = 0, sb = 0;
-        for (int c = 0; c < 32 && (t << 5) + c < nw; ++c) {
-            if (KA[(t << 5) + c]) sa |= 1u << c;
-            if (KB[(t << 5) + c]) sb |= 1u << c;
-        }
-        KA1[t] = sa;
-        KB1[t] = sb;
-    }
-    // window rank h: thread t counts the marks of words [w0, w1)
-    const int per = (nw + blockDim.x - 1) / blockDim.x;
-    const int w0 = min(nw, (int)threadIdx.x * per), w1 = min(nw, w0 + per);
-    int ca = 0, cb = 0;
-    for (int w = w0; w < w1; ++w) { ca += __popc(KA[w]); cb += __popc(KB[w]); }
-    scan[threadIdx.x] = ca + cb;
-    scan[blockDim.x + threadIdx.x] = ca;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int acc = 0, acca = 0;
-        for (int t = 0; t < (int)blockDim.x; ++t) {
-            const int c = scan[t], a = scan[blockDim.x + t];
-            scan[t] = acc; scan[blockDim.x + t] = acca;
-            acc += c; acca += a;
-        }
-    }
-    __syncthreads();
-    {
-        int before = scan[threadIdx.x], beforeA = scan[blockDim.x + threadIdx.x];
-        if (before <= h && h < before + ca + cb) {
-            // the element of window rank h lies in this thread's words
-            for (int w = w0; w < w1; ++w) {
-                const uint32_t any = KA[w] | KB[w];
-                const int c = __popc(any);
-                if (before + c > h) {
-                    uint32_t m = any;
-                    for (int j = h - before; j > 0; --j) m &= m - 1;   // drop the lower ones
-                    const int bit = __ffs(m) - 1;
-                    const int T = (w << 5) + bit;
-                    const int sA = beforeA + __popc(KA[w] & ((1u << bit) - 1u));
-                    sh_state[0] = T;
-                    sh_state[1] = sA;
-                    break;
+        const int pos = (int)(id & ~kBFlag);
+        return l == 0 ? (!isB && pos >= i0) : (isB && pos < i0);
+    };
+
+    // ---- pass 1: per-warp counts, first and last kept rank of each list ----
+    int cnt[2] = {0, 0}, first[2] = {-1, -1}, last[2] = {-1, -1};
+    for (int cb = c0; cb < c1; cb += kAhead) {
+        uint32_t ids[kAhead];
+        load(cb, ids);
+#pragma unroll
+        for (int j = 0; j < kAhead; ++j) {
+            const int c = cb + j;
+            if (c >= c1) break;
+            const uint32_t kb[2] = {__ballot_sync(kFull, kept(ids[j], 0)), __ballot_sync(kFull, kept(ids[j], 1))};
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                if (kb[l]) {
+                    if (first[l] < 0) first[l] = (c << 5) + __ffs(kb[l]) - 1;
+                    last[l] = (c << 5) + 31 - __clz(kb[l]);
+                    cnt[l] += __popc(kb[l]);
                 }
-                before += c;
-                beforeA += __popc(KA[w]);
             }
         }
     }
-    __syncthreads();
-    // lists of the window in rank-node space: a kept node's neighbours are the
-    // nearest kept ranks of its own block; sentinels SA = 2k, SB = 2k+1
-    uint2* Lq = p.lists + sid * p.LN;
-    const uint32_t SA = 2u * (uint32_t)k, SB = SA + 1u;
-    if (threadIdx.x == 0) {
-        const int T = sh_state[0], sA = sh_state[1];
-        const int fa = bits_first_from(KA, KA1, nw, ns, T), fb = bits_first_from(KB, KB1, nw, ns, T);
-        p.seg[sid] = make_int4(fa >= 0 ? fa : (int)SA, fb >= 0 ? fb : (int)SB, sA, h - sA);
-        const int a0 = bits_first_from(KA, KA1, nw, ns, 0), a1 = bits_last_before(KA, KA1, nw, tot);
-        const int b0 = bits_first_from(KB, KB1, nw, ns, 0), b1 = bits_last_before(KB, KB1, nw, tot);
-        Lq[SA] = make_uint2(a0 >= 0 ? (uint32_t)a0 : SA, a1 >= 0 ? (uint32_t)a1 : SA);
-        Lq[SB] = make_uint2(b0 >= 0 ? (uint32_t)b0 : SB, b1 >= 0 ? (uint32_t)b1 : SB);
+    if (lane == 0) {
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            s_cnt[l][warp] = cnt[l];
+            s_first[l][warp] = first[l];
+            s_last[l][warp] = last[l];
+        }
     }
-    for (int r = threadIdx.x; r < tot; r += blockDim.x) {
-        const uint32_t bit = 1u << (r & 31);
-        const bool inA = (KA[r >> 5] & bit) != 0, inB = (KB[r >> 5] & bit) != 0;
-        if (!inA && !inB) continue;                  // not in the window: never read
-        const uint32_t* W = inA ? KA : KB;
-        const uint32_t* W1 = inA ? KA1 : KB1;
-        const uint32_t sent = inA ? SA : SB;
-        const int nx = bits_first_from(W, W1, nw, ns, r + 1);
-        const int pv = bits_last_before(W, W1, nw, r);
-        Lq[r] = make_uint2(nx >= 0 ? (uint32_t)nx : sent, pv >= 0 ? (uint32_t)pv : sent);
+    __syncthreads();
+    // carries into this warp's ranks, and the lists' ends (sentinel links)
+    int run[2] = {-1, -1}, base[2] = {0, 0}, lastAll[2] = {-1, -1}, firstAll[2] = {-1, -1};
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        for (int w = 0; w < kW; ++w) {
+            if (w < warp) {
+                base[l] += s_cnt[l][w];
+                if (s_last[l][w] >= 0) run[l] = s_last[l][w];
+            }
+            if (s_last[l][w] >= 0) lastAll[l] = s_last[l][w];
+            if (firstAll[l] < 0) firstAll[l] = s_first[l][w];
+        }
+    }
+    if (threadIdx.x == 0) {
+        // a list's last node has its sentinel as next, and the sentinel has
+        // that node as prev (the sentinel's next is written in pass 2 by the
+        // list's first node, or here when the list is empty)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const uint32_t sent = l == 0 ? SA : SB;
+            if (lastAll[l] >= 0) NX[2 * lastAll[l]] = sent;
+            NX[2 * sent + 1] = lastAll[l] >= 0 ? (uint32_t)lastAll[l] : sent;
+            if (firstAll[l] < 0) NX[2 * sent] = sent;
+        }
+    }
+    // ---- pass 2: links, and the window's element of rank h ------------------
+    int nU = base[0] + base[1];                       // kept nodes of both lists before this chunk
+    int nA = base[0];
+    for (int cb = c0; cb < c1; cb += kAhead) {
+        uint32_t ids[kAhead];
+        load(cb, ids);
+#pragma unroll
+        for (int j = 0; j < kAhead; ++j) {
+            const int c = cb + j;
+            if (c >= c1) break;
+            const int r = (c << 5) + lane;
+            const uint32_t kb[2] = {__ballot_sync(kFull, kept(ids[j], 0)), __ballot_sync(kFull, kept(ids[j], 1))};
+            int pv[2];
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                const uint32_t m = kb[l] & below;
+                pv[l] = m ? (c << 5) + 31 - __clz(m) : run[l];
+                if ((kb[l] >> lane) & 1u) {
+                    const uint32_t sent = l == 0 ? SA : SB;
+                    const uint32_t pr = pv[l] >= 0 ? (uint32_t)pv[l] : sent;
+                    NX[2 * r + 1] = pr;                   // prev of r
+                    NX[2 * pr] = (uint32_t)r;             // next of its predecessor (or the sentinel)
+                }
+            }
+            const uint32_t u = kb[0] | kb[1];
+            const int cu = __popc(u);
+            if (nU <= h && h < nU + cu && ((u >> lane) & 1u) && __popc(u & below) == h - nU) {
+                s_res[0] = nA + __popc(kb[0] & below);   // s_A: kept A ranks below T
+                s_res[1] = pv[0];                         // last kept A rank below T
+                s_res[2] = pv[1];
+            }
+#pragma unroll
+            for (int l = 0; l < 2; ++l)
+                if (kb[l]) run[l] = (c << 5) + 31 - __clz(kb[l]);
+            nU += cu;
+            nA += __popc(kb[0]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // m_A / m_B: the first kept node of each list at or above T, i.e. the
+        // next of the last kept node below T (or the sentinel's next)
+        const volatile uint32_t* vx = NX;
+        const int sA = s_res[0], pA = s_res[1], pB = s_res[2];
+        const uint32_t fa = vx[2 * (pA >= 0 ? (uint32_t)pA : SA)];
+        const uint32_t fb = vx[2 * (pB >= 0 ? (uint32_t)pB : SB)];
+        p.seg[sid] = make_int4((int)fa, (int)fb, sA, h - sA);
     }
 }
 
@@ -706,12 +749,6 @@ static size_t unwind_smem(int k, int* nw, int* ns)
     // bitset words; 256 scan counts; W, R, Rc (nw each) and W1 (ns)
     return 20ull * kUnwindRun + 4ull * (32 * 32 + 256) + 4ull * (3 * (size_t)*nw + *ns);
 }
-static size_t seginit_smem(int k, int* nw, int* ns)
-{
-    *nw = (2 * k + 31) / 32;
-    *ns = (*nw + 31) / 32;
-    return 8ull * (size_t)(*nw + *ns) + 2 * 4 * 256 + 16;
-}
 
 size_t large_workspace_bytes(int64_t n, int k, bool wide)
 {
@@ -737,9 +774,7 @@ cudaError_t large_setup()
                                   (int)(8 * chunk_warp_bytes<uint32_t>())))) return e;
     if ((e = cudaFuncSetAttribute(large_chunk_sort<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(8 * chunk_warp_bytes<uint64_t>())))) return e;
-    if ((e = cudaFuncSetAttribute(large_unwind, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kMaxSmemBytes))) return e;
-    return cudaFuncSetAttribute(large_seginit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(large_unwind, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kMaxSmemBytes);
 }
 
@@ -765,9 +800,8 @@ static cudaError_t run_large(const LargeTable& tab, const int64_t* tot, int ntie
     }
     auto mark = [&](int idx) { if (evs) cudaEventRecord(evs[idx], stream); };
     auto grid = [](int64_t items, int per) { return (unsigned)((items + per - 1) / per); };
-    int unw, uns, snw, sns;
+    int unw, uns;
     const size_t usmem = unwind_smem(kmax, &unw, &uns);
-    const size_t ssmem = seginit_smem(kmax, &snw, &sns);
     cudaError_t e;
     mark(0);
     // phase 1: chunks, then merge tiers (ping-pong between the A and B buffers)
@@ -787,7 +821,7 @@ static cudaError_t run_large(const LargeTable& tab, const int64_t* tot, int ntie
         large_unwind<<<(unsigned)tot[kLUnwind], 256, usmem, stream>>>(tab);
         if ((e = launched()) != cudaSuccess) return e;
         mark(2);
-        large_seginit<<<(unsigned)tot[kLSeg], 256, ssmem, stream>>>(tab);
+        large_seginit<<<(unsigned)tot[kLSeg], 256, 0, stream>>>(tab);
         if ((e = launched()) != cudaSuccess) return e;
         large_chain<<<grid(tot[kLChain], 32), 32, 0, stream>>>(tab, tot[kLChain]);
         if ((e = launched()) != cudaSuccess) return e;
@@ -808,10 +842,8 @@ static bool large_prepare(LargeParams& p, const void* x, int64_t n, int k, int r
                           void* y, int32_t* argmed, char*& w, int64_t* tot)
 {
     if (k < 1 || k > kLargeMaxK || n < k || rank < 0 || rank >= k) return false;
-    int unw, uns, snw, sns;
-    if (unwind_smem(k, &unw, &uns) > (size_t)kMaxSmemBytes ||
-        seginit_smem(k, &snw, &sns) > (size_t)kMaxSmemBytes)
-        return false;
+    int unw, uns;
+    if (unwind_smem(k, &unw, &uns) > (size_t)kMaxSmemBytes) return false;
     const LargeShape sh = large_shape(n, k);
     p = LargeParams{};
     p.x = x; p.y = y; p.argmed = argmed;
