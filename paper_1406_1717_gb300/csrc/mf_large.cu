@@ -622,13 +622,23 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr)
 }
 
 // Section 6.2, steps i0 .. i1-1 of pair q: delete(A, i), undelete(B, i),
-// advance while s_A + s_B < h, print min(peek A, peek B).  Node numbers are
+// advance if s_A + s_B < h, print min(peek A, peek B).  Node numbers are
 // joint ranks, so "is small" and the peek comparison compare node numbers;
 // the sentinels 2k (A) and 2k+1 (B) rank above every element.
+// The thread keeps m_A and m_B with their nodes (next, prev) in registers.
+// Every node a step can move an m pointer to is m or one of its neighbours
+// at the start of the step, or the relinked node b itself (Section 5.3:
+// delete moves m to prev(m), or to next(m) when m itself goes; undelete
+// moves m to prev(m), which is b when b is relinked just before m; advance
+// moves m to next(m)).  So a step first stores its unlink and relink
+// (equations del / undo-del of Section 4), then loads the nodes of m_A, m_B
+// and their four neighbours, and the node the next step deletes: the loads
+// see the new links, their addresses depend only on the state at the start
+// of the step, and they form a single level of independent loads.
 __global__ void __launch_bounds__(32)
 large_chain(LargeTable tab, int64_t items)
 {
-    constexpr int kAhead = 8;                      // prefetch distance in steps
+    constexpr int kAhead = 8;                      // L2 prefetch distance in steps
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= items) return;
     int64_t sid;
@@ -639,7 +649,6 @@ large_chain(LargeTable tab, int64_t items)
     const int i0 = s * p.L;
     if (i0 >= NB) return;
     const int i1 = min(i0 + p.L, NB);
-    const int h = p.h;
     uint2* Lq = p.lists + sid * p.LN;
     uint32_t* NXp = reinterpret_cast<uint32_t*>(Lq);       // next of node r at [2r], prev at [2r+1]
     const uint32_t* JA = p.ja + q * p.kp;
@@ -647,51 +656,71 @@ large_chain(LargeTable tab, int64_t items)
     const uint2* UL = p.ulink + (q + 1) * p.kp;
     uint32_t* OUT = p.out + q * p.kp;
     const int4 st = p.seg[sid];
-    uint32_t mA = (uint32_t)st.x, mB = (uint32_t)st.y;
-    int sA = st.z, sB = st.w;
-    for (int t = i0; t < min(i0 + kAhead, i1); ++t) prefetch_l2(Lq + __ldg(JA + t));
 #ifdef MF_DEBUG
     const uint32_t nmax = 2u * (uint32_t)p.k + 1u;          // sentinel B, the largest node
     auto node = [&](uint32_t r, uint32_t site) { return MF_CHECK(r <= nmax, site, r) ? r : nmax; };
 #else
     auto node = [](uint32_t r, uint32_t) { return r; };
 #endif
-    mA = node(mA, 301);
-    mB = node(mB, 301);
+    uint32_t mA = node((uint32_t)st.x, 301), mB = node((uint32_t)st.y, 301);
+    int sA = st.z;                                 // s_B = h - s_A at every step boundary
+    for (int t = i0; t < min(i0 + kAhead, i1); ++t) prefetch_l2(Lq + __ldg(JA + t));
+    uint2 wmA = Lq[mA], wmB = Lq[mB];
+    uint32_t a = node(__ldg(JA + i0), 301);
+    uint2 La = Lq[a];
     for (int i = i0; i < i1; ++i) {
-        const uint32_t a = node(__ldg(JA + i), 301), b = node(__ldg(JB + i), 301);
-        uint2 u = __ldg(UL + i);
-        u.x = node(u.x, 301);
-        u.y = node(u.y, 301);
+        const uint32_t b = node(__ldg(JB + i), 301);
+        const uint2 u = __ldg(UL + i);
+        const uint32_t pb = node(u.x, 301), nb = node(u.y, 301);   // b's unwind links
+        const uint32_t an = i + 1 < i1 ? node(__ldg(JA + i + 1), 301) : a;
         if (i + kAhead < i1) prefetch_l2(Lq + __ldg(JA + i + kAhead));
-        const uint2 La = Lq[a];
-        const uint2 LmA = Lq[mA];
-        const uint2 LmB = Lq[mB];
-        // delete(A, i): unlink node a, then keep s_A and m consistent
+        const uint32_t pm = node(wmA.y, 301), nm = node(wmA.x, 301);
+        const uint32_t pmB = node(wmB.y, 301), nmB = node(wmB.x, 301);
+        // -------- relinks: delete(A, i) unlinks a, undelete(B, i) relinks b ----
         const uint32_t na = node(La.x, 301), pa = node(La.y, 301);
-        NXp[2 * pa] = na;
-        NXp[2 * na + 1] = pa;
-        if (a < mA) {
-            --sA;
-        } else {
-            uint32_t pvm = (mA == na) ? pa : node(LmA.y, 301);   // prev of m after the unlink
-            if (mA == a) { mA = na; pvm = pa; }
-            if (sA > 0) { mA = pvm; --sA; }
-        }
-        // undelete(B, i): relink node b between its unwind links
-        Lq[b] = make_uint2(u.y, u.x);
-        NXp[2 * u.x] = b;
-        NXp[2 * u.y + 1] = b;
-        if (b < mB) mB = (mB == u.y) ? b : node(LmB.y, 301);
-        // advance the smaller peek while s_A + s_B < h
-        if (sA + sB < h) {
-            if (mA < mB) { mA = node(Lq[mA].x, 301); ++sA; }
-            else         { mB = node(Lq[mB].x, 301); ++sB; }
-        }
-        // Section 6.3: s_A + s_B = h after every step; the median is an element
-        (void)MF_CHECK(sA >= 0 && sB >= 0 && sA + sB == h, 302, (uint64_t)(uint32_t)sA << 32 | (uint32_t)sB);
+        NXp[2 * pa] = na;                                   // next[prev[a]] <- next[a]
+        NXp[2 * na + 1] = pa;                               // prev[next[a]] <- prev[a]
+        const uint2 wb = make_uint2(nb, pb);
+        Lq[b] = wb;
+        NXp[2 * pb] = b;                                    // next[prev[b]] <- b
+        NXp[2 * nb + 1] = b;                                // prev[next[b]] <- b
+        // -------- the candidates' nodes, after the relinks ------------------------
+        const uint2 wA0 = Lq[mA], wpm = Lq[pm], wnm = Lq[nm];
+        const uint2 wB0 = Lq[mB], wpmB = Lq[pmB], wnmB = Lq[nmB];
+        const uint2 Lan = Lq[an];
+        // -------- delete(A, i): the m pointer and s -------------------------------
+        const bool small = a < mA;
+        const bool isM = a == mA;
+        const bool sApos = sA > 0;
+        const bool toP = !small && sApos, toN = !small && !sApos && isM;
+        const uint32_t mA1 = toP ? pm : (toN ? nm : mA);
+        const uint2 wA1 = toP ? wpm : (toN ? wnm : wA0);
+        sA -= (small || sApos) ? 1 : 0;                     // s <- max(0, s - 1)
+        const bool nxtOld = toP && !isM;                    // next of prev(m) is m itself
+        const uint32_t aNode = nxtOld ? mA : nm;
+        const uint2 aWord = nxtOld ? wA0 : wnm;
+        // -------- undelete(B, i): the m pointer -------------------------------------
+        const bool smallB = b < mB;                         // small: m <- prev[m]
+        const bool justB = nb == mB;                        // b relinked just before m
+        const uint32_t mB1 = smallB ? (justB ? b : pmB) : mB;
+        const uint2 wB1 = smallB ? (justB ? wb : wpmB) : wB0;
+        const bool afterB = pb == mB;                       // b relinked just after m
+        const uint32_t bNode = smallB ? mB : (afterB ? b : nmB);
+        const uint2 bWord = smallB ? wB0 : (afterB ? wb : wnmB);
+        // -------- advance the list whose first large element is smaller -------------
+        const bool aA = mA1 < mB1;
+        const bool advA = sApos && aA, advB = sApos && !aA;
+        mA = advA ? aNode : mA1;
+        wmA = advA ? aWord : wA1;
+        mB = advB ? bNode : mB1;
+        wmB = advB ? bWord : wB1;
+        sA += advA ? 1 : 0;
+        // Section 6.3: 0 <= s_A <= h after every step; the median is an element
+        (void)MF_CHECK(sA >= 0 && sA <= p.h, 302, sA);
         (void)MF_CHECK((mA < mB ? mA : mB) < 2u * (uint32_t)p.k, 303, mA < mB ? mA : mB);
         OUT[i] = mA < mB ? mA : mB;                        // joint rank of the median
+        a = an;
+        La = Lan;
     }
 }
 
