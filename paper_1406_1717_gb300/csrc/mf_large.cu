@@ -335,12 +335,20 @@ large_unwind(LargeTable tab)
     const uint32_t sentB = 2u * (uint32_t)p.k + 1u;
     const uint32_t* jrs = p.jrs + (b - 1) * p.kp;
     {
+        // eight words per warp at a time: their loads in flight together
         const int first = run0 * kUnwindRun;
-        for (int w = warp; w < nw; w += nwarp) {
-            const int r = (w << 5) + lane;
-            const bool set = r < NB && (int)__ldg(vs + base + r) < first;
-            const uint32_t word = __ballot_sync(kFull, set);
-            if (lane == 0) W[w] = word;
+        for (int w0 = warp; w0 < nw; w0 += 8 * nwarp) {
+            uint32_t pos[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int r = ((w0 + j * nwarp) << 5) + lane;
+                pos[j] = w0 + j * nwarp < nw && r < NB ? __ldg(vs + base + r) : 0xffffffffu;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t word = __ballot_sync(kFull, pos[j] < (uint32_t)first);
+                if (lane == 0 && w0 + j * nwarp < nw) W[w0 + j * nwarp] = word;
+            }
         }
         __syncthreads();
         for (int sI = tid; sI < ns; sI += blockDim.x) {
@@ -449,14 +457,29 @@ large_unwind(LargeTable tab)
         __syncthreads();
         // ranks -> rank nodes of pair b-1 (B's t-th smallest is node jrs[t]);
         // the run's ranks join W for the next run
-        for (int t = tid; t < len; t += blockDim.x) {
-            const int2 q = pp[t];
-            const uint32_t pv = q.x >= 0 ? __ldg(jrs + q.x) : sentB;
-            const uint32_t nx = q.y >= 0 ? __ldg(jrs + q.y) : sentB;
-            p.ulink[base + i0 + t] = make_uint2(pv, nx);
-            const uint32_t r = rr[t];
-            atomicOr(&W[r >> 5], 1u << (r & 31));
-            atomicOr(&W1[r >> 10], 1u << ((r >> 5) & 31));
+        static_assert(kUnwindRun <= 4 * 256, "four positions per thread cover a run");
+        {
+            uint2 o[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {                // loads first, four positions in flight
+                const int t = tid + u * (int)blockDim.x;
+                o[u] = make_uint2(sentB, sentB);
+                if (t < len) {
+                    const int2 q = pp[t];
+                    if (q.x >= 0) o[u].x = __ldg(jrs + q.x);
+                    if (q.y >= 0) o[u].y = __ldg(jrs + q.y);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = tid + u * (int)blockDim.x;
+                if (t < len) {
+                    p.ulink[base + i0 + t] = o[u];
+                    const uint32_t r = rr[t];
+                    atomicOr(&W[r >> 5], 1u << (r & 31));
+                    atomicOr(&W1[r >> 10], 1u << ((r >> 5) & 31));
+                }
+            }
         }
         __syncthreads();
     }
