@@ -875,7 +875,17 @@ static cudaError_t run_large(const LargeTable& tab, const int64_t* tot, int ntie
         mark(2);
         large_seginit<<<(unsigned)tot[kLSeg], 256, 0, stream>>>(tab);
         if ((e = launched()) != cudaSuccess) return e;
-        large_chain<<<grid(tot[kLChain], 32), 32, 0, stream>>>(tab, tot[kLChain]);
+        // chains per CTA: the fewest (a power of two up to 32) that keep the
+        // CTAs within 24 per SM.  A chain's node accesses do not coalesce with
+        // other chains', so spreading them over every SM and over more warps
+        // spreads their L1 traffic (GB300, n = 10^7: k = 100,001, 3,168
+        // chains, 4.49 ms with 32 per CTA, 3.99 ms with one; k = 20,001,
+        // 9,980 chains, best with 4 per CTA)
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int cpc = 1;
+        while (cpc < 32 && (tot[kLChain] + cpc - 1) / cpc > 24ll * sms) cpc <<= 1;
+        large_chain<<<grid(tot[kLChain], cpc), cpc, 0, stream>>>(tab, tot[kLChain]);
         if ((e = launched()) != cudaSuccess) return e;
     } else {
         mark(1);
