@@ -20,7 +20,7 @@
 //                     before the run
 //   large_seginit     rebuilds the lists before step i0 of a pair (Section 6.3
 //                     invariant: S_A u S_B are the h smallest of the window)
-//                     in two coalesced passes over the pair's merged order
+//                     in one coalesced pass over the pair's merged order
 //   large_chain       the steps i0 .. i1-1 of Section 6.2 from that state,
 //                     one thread per (pair, segment), lists in global memory
 //   large_epilogue    node -> input element, y / argmed
@@ -487,24 +487,29 @@ large_unwind(LargeTable tab)
 
 // One CTA per (pair q, segment s): the state before step i0 = s L (Section
 // 6.3: S_A u S_B are the h smallest elements of the window A[i0 .. k) u
-// B[0 .. i0)), from the pair's merged order M in two coalesced passes.  Joint
+// B[0 .. i0)), from the pair's merged order M in one coalesced pass.  Joint
 // rank r is kept in A's list if it is an element of A at a position >= i0,
 // in B's list if it is an element of B at a position < i0; a kept node's
 // neighbours are the nearest kept ranks of its own list (sentinels SA = 2k,
-// SB = 2k + 1).  Pass 1: every warp counts the kept nodes of its range of
-// ranks (32 per ballot) and notes its first and last.  Pass 2: every kept
-// node writes its prev (the highest kept rank of its list below it in the
-// same 32, else the carry: the last kept rank before those 32) and, as its
-// predecessor's next, itself; the warp whose ranks hold the window's element
-// of rank h records s_A and the last kept rank of each list below it.  Both
-// passes keep eight loads of M in flight per lane.
+// SB = 2k + 1).  Each warp takes a range of ranks, 32 per ballot: a kept
+// node's prev is the highest kept rank of its list below it in the same 32,
+// else the last one in the warp's earlier ranks, and the node writes itself
+// as that node's next.  The first kept node of each list in a warp's range
+// is linked after a barrier, to the last one of the warps before it.  Every
+// 32 ballots a warp saves its counts and last kept nodes; the warp whose
+// ranks hold the window's element of rank h then finds it by rescanning at
+// most 32 ballots from a saved point, and with it s_A and the last kept node
+// of each list below it.  Eight loads of M are in flight per lane.
 __global__ void __launch_bounds__(256)
 large_seginit(LargeTable tab)
 {
     constexpr int kW = 8;                          // warps per CTA
     constexpr int kAhead = 8;                      // chunks of 32 ranks loaded at once
+    constexpr int kCk = 32;                        // chunks between saved points
+    constexpr int kMaxCk = (2 * kLargeMaxK + 2 + 32 * kW * kCk - 1) / (32 * kW * kCk);
     constexpr uint32_t kNone = 0xffffffffu;        // past the window: neither list
     __shared__ int s_cnt[2][kW], s_first[2][kW], s_last[2][kW];
+    __shared__ int4 s_ck[kW][kMaxCk];              // before chunk c0 + 32 j: (#A, #both, last A, last B)
     __shared__ int s_res[3];                       // s_A, last kept A / B rank below T
     int64_t sid;
     const LargeParams p = find_large(tab, kLSeg, blockIdx.x, &sid);
@@ -535,8 +540,9 @@ large_seginit(LargeTable tab)
         return l == 0 ? (!isB && pos >= i0) : (isB && pos < i0);
     };
 
-    // ---- pass 1: per-warp counts, first and last kept rank of each list ----
-    int cnt[2] = {0, 0}, first[2] = {-1, -1}, last[2] = {-1, -1};
+    // ---- the pass: links within the warp's ranks, counts, saved points ----
+    int run[2] = {-1, -1}, first[2] = {-1, -1};
+    int nA = 0, nU = 0;                                // kept nodes before the chunk (this warp)
     for (int cb = c0; cb < c1; cb += kAhead) {
         uint32_t ids[kAhead];
         load(cb, ids);
@@ -544,87 +550,91 @@ large_seginit(LargeTable tab)
         for (int j = 0; j < kAhead; ++j) {
             const int c = cb + j;
             if (c >= c1) break;
+            if (((c - c0) & (kCk - 1)) == 0 && lane == 0)
+                s_ck[warp][(c - c0) / kCk] = make_int4(nA, nU, run[0], run[1]);
+            const int r = (c << 5) + lane;
             const uint32_t kb[2] = {__ballot_sync(kFull, kept(ids[j], 0)), __ballot_sync(kFull, kept(ids[j], 1))};
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
-                if (kb[l]) {
-                    if (first[l] < 0) first[l] = (c << 5) + __ffs(kb[l]) - 1;
-                    last[l] = (c << 5) + 31 - __clz(kb[l]);
-                    cnt[l] += __popc(kb[l]);
+                if (!kb[l]) continue;
+                const uint32_t m = kb[l] & below;
+                const int pv = m ? (c << 5) + 31 - __clz(m) : run[l];
+                if (((kb[l] >> lane) & 1u) && pv >= 0) {
+                    NX[2 * r + 1] = (uint32_t)pv;         // prev of r
+                    NX[2 * pv] = (uint32_t)r;             // next of its predecessor
                 }
+                if (first[l] < 0) first[l] = (c << 5) + __ffs(kb[l]) - 1;
+                run[l] = (c << 5) + 31 - __clz(kb[l]);
             }
+            nA += __popc(kb[0]);
+            nU += __popc(kb[0] | kb[1]);
         }
+    }
+    if (lane == 0) {
+        s_cnt[0][warp] = nA;
+        s_cnt[1][warp] = nU;
+        s_first[0][warp] = first[0];
+        s_first[1][warp] = first[1];
+        s_last[0][warp] = run[0];
+        s_last[1][warp] = run[1];
+    }
+    __syncthreads();
+    // ---- links across warps and to the sentinels (lane 0 of each warp) ----
+    int baseA = 0, baseU = 0, carry[2] = {-1, -1};
+    for (int w = 0; w < warp; ++w) {
+        baseA += s_cnt[0][w];
+        baseU += s_cnt[1][w];
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+            if (s_last[l][w] >= 0) carry[l] = s_last[l][w];
     }
     if (lane == 0) {
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
-            s_cnt[l][warp] = cnt[l];
-            s_first[l][warp] = first[l];
-            s_last[l][warp] = last[l];
-        }
-    }
-    __syncthreads();
-    // carries into this warp's ranks, and the lists' ends (sentinel links)
-    int run[2] = {-1, -1}, base[2] = {0, 0}, lastAll[2] = {-1, -1}, firstAll[2] = {-1, -1};
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-        for (int w = 0; w < kW; ++w) {
-            if (w < warp) {
-                base[l] += s_cnt[l][w];
-                if (s_last[l][w] >= 0) run[l] = s_last[l][w];
-            }
-            if (s_last[l][w] >= 0) lastAll[l] = s_last[l][w];
-            if (firstAll[l] < 0) firstAll[l] = s_first[l][w];
-        }
-    }
-    if (threadIdx.x == 0) {
-        // a list's last node has its sentinel as next, and the sentinel has
-        // that node as prev (the sentinel's next is written in pass 2 by the
-        // list's first node, or here when the list is empty)
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
             const uint32_t sent = l == 0 ? SA : SB;
-            if (lastAll[l] >= 0) NX[2 * lastAll[l]] = sent;
-            NX[2 * sent + 1] = lastAll[l] >= 0 ? (uint32_t)lastAll[l] : sent;
-            if (firstAll[l] < 0) NX[2 * sent] = sent;
+            if (first[l] >= 0) {                         // this warp's first kept node
+                const uint32_t pr = carry[l] >= 0 ? (uint32_t)carry[l] : sent;
+                NX[2 * first[l] + 1] = pr;
+                NX[2 * pr] = (uint32_t)first[l];
+            }
+            if (warp == kW - 1) {                         // the list's last node, the sentinel's prev
+                int lastAll = carry[l];
+                if (run[l] >= 0) lastAll = run[l];
+                if (lastAll >= 0) NX[2 * lastAll] = sent;
+                NX[2 * sent + 1] = lastAll >= 0 ? (uint32_t)lastAll : sent;
+                if (lastAll < 0) NX[2 * sent] = sent;
+            }
         }
     }
-    // ---- pass 2: links, and the window's element of rank h ------------------
-    int nU = base[0] + base[1];                       // kept nodes of both lists before this chunk
-    int nA = base[0];
-    for (int cb = c0; cb < c1; cb += kAhead) {
-        uint32_t ids[kAhead];
-        load(cb, ids);
-#pragma unroll
-        for (int j = 0; j < kAhead; ++j) {
-            const int c = cb + j;
-            if (c >= c1) break;
+    // ---- the window's element of rank h: the warp holding it rescans ------
+    if (baseU <= h && h < baseU + nU) {                 // warp-uniform
+        int j = 0;
+        const int nck = (c1 - c0 + kCk - 1) / kCk;
+        while (j + 1 < nck && s_ck[warp][j + 1].y <= h - baseU) ++j;
+        const int4 ck = s_ck[warp][j];
+        int cA = ck.x, cU = ck.y, rl[2] = {ck.z, ck.w};
+        bool found = false;
+        for (int c = c0 + j * kCk; c < c1 && !found; ++c) {
             const int r = (c << 5) + lane;
-            const uint32_t kb[2] = {__ballot_sync(kFull, kept(ids[j], 0)), __ballot_sync(kFull, kept(ids[j], 1))};
-            int pv[2];
-#pragma unroll
-            for (int l = 0; l < 2; ++l) {
-                const uint32_t m = kb[l] & below;
-                pv[l] = m ? (c << 5) + 31 - __clz(m) : run[l];
-                if ((kb[l] >> lane) & 1u) {
-                    const uint32_t sent = l == 0 ? SA : SB;
-                    const uint32_t pr = pv[l] >= 0 ? (uint32_t)pv[l] : sent;
-                    NX[2 * r + 1] = pr;                   // prev of r
-                    NX[2 * pr] = (uint32_t)r;             // next of its predecessor (or the sentinel)
-                }
-            }
-            const uint32_t u = kb[0] | kb[1];
+            const uint32_t id = r < tot ? __ldg(M + r) : kNone;
+            const uint32_t kb0 = __ballot_sync(kFull, kept(id, 0)), kb1 = __ballot_sync(kFull, kept(id, 1));
+            const uint32_t u = kb0 | kb1;
             const int cu = __popc(u);
-            if (nU <= h && h < nU + cu && ((u >> lane) & 1u) && __popc(u & below) == h - nU) {
-                s_res[0] = nA + __popc(kb[0] & below);   // s_A: kept A ranks below T
-                s_res[1] = pv[0];                         // last kept A rank below T
-                s_res[2] = pv[1];
+            if (h - baseU < cU + cu) {                    // warp-uniform: T is in this chunk
+                if (((u >> lane) & 1u) && __popc(u & below) == h - baseU - cU) {
+                    s_res[0] = baseA + cA + __popc(kb0 & below);   // s_A: kept A ranks below T
+                    const uint32_t m0 = kb0 & below, m1 = kb1 & below;
+                    const int pA = m0 ? (c << 5) + 31 - __clz(m0) : rl[0];
+                    const int pB = m1 ? (c << 5) + 31 - __clz(m1) : rl[1];
+                    s_res[1] = pA >= 0 ? pA : carry[0];             // last kept A rank below T
+                    s_res[2] = pB >= 0 ? pB : carry[1];
+                }
+                found = true;
             }
-#pragma unroll
-            for (int l = 0; l < 2; ++l)
-                if (kb[l]) run[l] = (c << 5) + 31 - __clz(kb[l]);
-            nU += cu;
-            nA += __popc(kb[0]);
+            if (kb0) rl[0] = (c << 5) + 31 - __clz(kb0);
+            if (kb1) rl[1] = (c << 5) + 31 - __clz(kb1);
+            cA += __popc(kb0);
+            cU += cu;
         }
     }
     __syncthreads();
