@@ -305,7 +305,11 @@ large_jrank(LargeTable tab, int64_t items)
 //    of the lanes before it (an exclusive OR-scan over lanes), as the fused
 //    sort kernel does for a whole block.
 // The ranks are then turned into nodes.
-__global__ void __launch_bounds__(256)
+// Three CTAs per SM (80 registers; shared memory allows three): a CTA's
+// run-by-run phases leave most of its warps at barriers while warp 0 walks,
+// so a third CTA fills the SM (GB300, n = 10^7, k = 100,001: 0.95 -> 0.72 ms,
+// despite 200 bytes of spills).
+__global__ void __launch_bounds__(256, 3)
 large_unwind(LargeTable tab)
 {
     extern __shared__ __align__(16) uint32_t sw[];
@@ -508,7 +512,7 @@ large_seginit(LargeTable tab)
     constexpr int kCk = 32;                        // chunks between saved points
     constexpr int kMaxCk = (2 * kLargeMaxK + 2 + 32 * kW * kCk - 1) / (32 * kW * kCk);
     constexpr uint32_t kNone = 0xffffffffu;        // past the window: neither list
-    __shared__ int s_cnt[2][kW], s_first[2][kW], s_last[2][kW];
+    __shared__ int s_cnt[2][kW], s_last[2][kW];
     __shared__ int4 s_ck[kW][kMaxCk];              // before chunk c0 + 32 j: (#A, #both, last A, last B)
     __shared__ int s_res[3];                       // s_A, last kept A / B rank below T
     int64_t sid;
@@ -573,8 +577,6 @@ large_seginit(LargeTable tab)
     if (lane == 0) {
         s_cnt[0][warp] = nA;
         s_cnt[1][warp] = nU;
-        s_first[0][warp] = first[0];
-        s_first[1][warp] = first[1];
         s_last[0][warp] = run[0];
         s_last[1][warp] = run[1];
     }
