@@ -82,7 +82,7 @@ enum {
     kLChunk = 0,          // warp: (block, chunk)
     kLMerge0 = 1,         // thread: 4 outputs of merge tier t (kLMerge0 + t)
     kLRanks = 9,          // thread: (block, sorted index)
-    kLJrank = 10,         // thread: (pair, element of A or B)
+    kLJrank = 10,         // thread: (pair, run of kJrankRun merged outputs)
     kLUnwind = 11,        // CTA: (block >= 1, run of kUnwindRun positions)
     kLSeg = 12,           // CTA: (pair, segment)
     kLChain = 13,         // thread: (pair, segment)
@@ -253,8 +253,12 @@ large_ranks(LargeTable tab, int64_t items)
     p.rnk[b * p.kp + vs[b * p.kp + t]] = (uint32_t)t;
 }
 
-// joint rank of every element of pair q (A = block q, B = block q+1):
-// A's t-th smallest -> t + #{B keys < key}; B's u-th -> u + #{A keys <= key}
+// Joint ranks of pair q (A = block q, B = block q+1) by a merge of the two
+// sorted blocks, A first on equal keys: A's t-th smallest gets t + #{B keys
+// < key}, B's u-th u + #{A keys <= key}.  A thread takes kJrankRun
+// consecutive outputs of the merged order: one merge-path search for where
+// they start (Green, McColl & Bader 2012), then a sequential merge.
+constexpr int kJrankRun = 8;
 template <typename KeyT>
 __global__ void __launch_bounds__(256)
 large_jrank(LargeTable tab, int64_t items)
@@ -265,28 +269,34 @@ large_jrank(LargeTable tab, int64_t items)
     const LargeParams p = find_large(tab, kLJrank, g, &gid);
     const KeyT* __restrict__ ks = reinterpret_cast<const KeyT*>(p.ksort);
     const uint32_t* __restrict__ vs = p.vsort;
-    const int64_t per_pair = 2 * p.kp;
+    const int64_t per_pair = 2 * p.kp / kJrankRun;
     const int64_t q = gid / per_pair;
-    const int e = (int)(gid - q * per_pair);
-    const int NA = p.k, NB = block_len(p, q + 1);
-    const int64_t abase = q * p.kp, bbase = (q + 1) * p.kp;
-    uint32_t* M = p.M + q * per_pair;
-    if (e < NA) {
-        const KeyT key = ks[abase + e];
-        int lo = 0, hi = NB;
-        while (lo < hi) { const int mid = (lo + hi) >> 1; if (ks[bbase + mid] < key) lo = mid + 1; else hi = mid; }
-        const uint32_t pos = vs[abase + e];
-        M[e + lo] = pos;
-        p.ja[q * p.kp + pos] = (uint32_t)(e + lo);
-    } else if (e >= (int)p.kp && e - (int)p.kp < NB) {
-        const int u = e - (int)p.kp;
-        const KeyT key = ks[bbase + u];
-        int lo = 0, hi = NA;
-        while (lo < hi) { const int mid = (lo + hi) >> 1; if (ks[abase + mid] <= key) lo = mid + 1; else hi = mid; }
-        const uint32_t pos = vs[bbase + u];
-        M[u + lo] = kBFlag | pos;
-        p.jb[q * p.kp + pos] = (uint32_t)(u + lo);
-        p.jrs[q * p.kp + u] = (uint32_t)(u + lo);
+    const int NA = p.k, NB = block_len(p, q + 1), tot = NA + NB;
+    const int o0 = (int)(gid - q * per_pair) * kJrankRun;
+    if (o0 >= tot) return;
+    const int o1 = min(o0 + kJrankRun, tot);
+    const KeyT* KA = ks + q * p.kp;
+    const KeyT* KB = ks + (q + 1) * p.kp;
+    int lo = max(0, o0 - NB), hi = min(o0, NA);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (KA[mid] <= KB[o0 - 1 - mid]) lo = mid + 1; else hi = mid;
+    }
+    int ia = lo, ib = o0 - lo;
+    uint32_t* M = p.M + q * 2 * p.kp;
+    for (int o = o0; o < o1; ++o) {
+        if (ib >= NB || (ia < NA && KA[ia] <= KB[ib])) {
+            const uint32_t pos = vs[q * p.kp + ia];
+            M[o] = pos;
+            p.ja[q * p.kp + pos] = (uint32_t)o;
+            ++ia;
+        } else {
+            const uint32_t pos = vs[(q + 1) * p.kp + ib];
+            M[o] = kBFlag | pos;
+            p.jb[q * p.kp + pos] = (uint32_t)o;
+            p.jrs[q * p.kp + ib] = (uint32_t)o;
+            ++ib;
+        }
     }
 }
 
@@ -954,7 +964,7 @@ static bool large_prepare(LargeParams& p, const void* x, int64_t n, int k, int r
     for (int t = 0; t < p.ntier; ++t) cnt[kLMerge0 + t] = sh.nblocks * (sh.kp / 4);
     if (sh.npairs > 0) {
         cnt[kLRanks] = sh.nblocks * sh.kp;
-        cnt[kLJrank] = sh.npairs * 2 * sh.kp;
+        cnt[kLJrank] = sh.npairs * 2 * sh.kp / kJrankRun;
         cnt[kLUnwind] = (sh.nblocks - 1) *
                         (((k + kUnwindRun - 1) / kUnwindRun + kUnwindRunsPerCta - 1) / kUnwindRunsPerCta);
         cnt[kLSeg] = sh.npairs * sh.S;
