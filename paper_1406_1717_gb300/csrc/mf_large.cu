@@ -39,6 +39,7 @@
 #include <cstdint>
 #include "mf_device.cuh"
 #include "mf_internal.h"
+#include "mf_tilesort.cuh"
 
 namespace mf {
 
@@ -165,9 +166,11 @@ __device__ __forceinline__ int bits_last_before(const uint32_t* W, const uint32_
 // ---------------------------------------------------------------------------
 template <typename KeyT>
 __host__ __device__ constexpr size_t chunk_warp_bytes() { return (size_t)kChunk * (2 * sizeof(KeyT) + 4) + 1024; }
+static_assert(kChunk == kTileElems && 8 * kTileU64 <= (int)chunk_warp_bytes<uint32_t>(),
+              "a 4-byte chunk is one warp tile of composites");
 
 template <typename KeyT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 large_chunk_sort(LargeTable tab, int64_t items)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -189,6 +192,30 @@ large_chunk_sort(LargeTable tab, int64_t items)
     uint16_t* vb = va + kChunk;
     uint32_t* hist = reinterpret_cast<uint32_t*>(vb + kChunk);
     const KeyT* xs = reinterpret_cast<const KeyT*>(p.x) + b * (int64_t)p.k + lo;
+    if constexpr (sizeof(KeyT) == 4) {
+        // 4-byte keys: the warp merge sort of composites key : index in the
+        // chunk (10 bits), which orders equal keys by position
+        uint64_t* T = reinterpret_cast<uint64_t*>(ws);
+        uint64_t v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {                  // coalesced: the network takes any 32
+            const int t = lane + 32 * i;
+            v[i] = t < cnt ? ((uint64_t)to_key(__ldg(xs + t), p.is_float) << 10) | (uint32_t)t : kPadComp;
+        }
+        tile_sort(T, v, lane);
+        const int64_t o = b * p.kp + lo;
+        KeyT* keys = reinterpret_cast<KeyT*>(p.keyA);
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+            const int t = lane + 32 * i;
+            if (t < cnt) {
+                const uint64_t c = T[tix(t)];
+                keys[o + t] = (KeyT)(c >> 10);
+                p.valA[o + t] = (uint32_t)lo + (uint32_t)(c & 1023u);
+            }
+        }
+        return;
+    }
     for (int t = lane; t < cnt; t += 32) { ka[t] = to_key(__ldg(xs + t), p.is_float); va[t] = (uint16_t)t; }
     __syncwarp();
     warp_sort_group<KeyT>(ka, va, kb, vb, cnt, 0, kChunk, 1, hist);
