@@ -225,7 +225,8 @@ large_chunk_sort(LargeTable tab, int64_t items)
 }
 
 // sorted runs [l0, l0+R) and [l0+R, l0+2R) of every block -> one run; each
-// thread writes 4 consecutive outputs after a merge-path search
+// thread writes kMergeOut consecutive outputs after a merge-path search
+constexpr int kMergeOut = 4;             // 8, 16, 32 measured slower (GB300, k = 100,001)
 template <typename KeyT>
 __global__ void __launch_bounds__(256)
 large_merge(LargeTable tab, int tier, int64_t items)
@@ -241,9 +242,9 @@ large_merge(LargeTable tab, int tier, int64_t items)
     const uint32_t* __restrict__ vin = odd ? p.valB : p.valA;
     uint32_t* __restrict__ vout = odd ? p.valA : p.valB;
     const int R = kChunk << tier;
-    const int per_block = (int)(p.kp / 4);
+    const int per_block = (int)(p.kp / kMergeOut);
     const int64_t b = gid / per_block;
-    const int o = (int)(gid - b * per_block) * 4;
+    const int o = (int)(gid - b * per_block) * kMergeOut;
     const int NB = block_len(p, b);
     if (o >= NB) return;
     const int64_t base = b * p.kp;
@@ -258,7 +259,7 @@ large_merge(LargeTable tab, int tier, int64_t items)
         if (KL[mid] <= KR[d - 1 - mid]) lo = mid + 1; else hi = mid;
     }
     int ia = lo, ib = d - lo;
-    const int oend = min(o + 4, NB);
+    const int oend = min(o + kMergeOut, NB);
     for (int q = o; q < oend; ++q) {
         const bool takeL = ib >= lenR || (ia < lenL && KL[ia] <= KR[ib]);
         if (takeL) { kout[base + q] = KL[ia]; vout[base + q] = vin[base + l0 + ia]; ++ia; }
@@ -988,7 +989,7 @@ static bool large_prepare(LargeParams& p, const void* x, int64_t n, int k, int r
     p.vsort = p.ntier & 1 ? p.valB : p.valA;
     int64_t cnt[15] = {0};
     cnt[kLChunk] = sh.nblocks * p.cpb;
-    for (int t = 0; t < p.ntier; ++t) cnt[kLMerge0 + t] = sh.nblocks * (sh.kp / 4);
+    for (int t = 0; t < p.ntier; ++t) cnt[kLMerge0 + t] = sh.nblocks * (sh.kp / kMergeOut);
     if (sh.npairs > 0) {
         cnt[kLRanks] = sh.nblocks * sh.kp;
         cnt[kLJrank] = sh.npairs * 2 * sh.kp / kJrankRun;
