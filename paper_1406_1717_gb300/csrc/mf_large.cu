@@ -225,7 +225,8 @@ large_chunk_sort(LargeTable tab, int64_t items)
 }
 
 // sorted runs [l0, l0+R) and [l0+R, l0+2R) of every block -> one run; each
-// thread writes kMergeOut consecutive outputs after a merge-path search
+// thread writes kMergeOut consecutive outputs after a merge-path search (2 was
+// slower too)
 constexpr int kMergeOut = 4;             // 8, 16, 32 measured slower (GB300, k = 100,001)
 template <typename KeyT>
 __global__ void __launch_bounds__(256)
@@ -286,7 +287,7 @@ large_ranks(LargeTable tab, int64_t items)
 // < key}, B's u-th u + #{A keys <= key}.  A thread takes kJrankRun
 // consecutive outputs of the merged order: one merge-path search for where
 // they start (Green, McColl & Bader 2012), then a sequential merge.
-constexpr int kJrankRun = 8;
+constexpr int kJrankRun = 4;             // 8 and 16 measured slower (GB300, k = 100,001)
 template <typename KeyT>
 __global__ void __launch_bounds__(256)
 large_jrank(LargeTable tab, int64_t items)
