@@ -40,6 +40,7 @@ UNIT = "Gsamples/s"
 WORKLOAD = "float32 Gaussian random walk, n=2^26, k=1001"
 HBM_FALLBACK_GBS = 6800.0
 KERNEL_SOURCES = ["paper_1406_1717_gb300/csrc/mf_device.cuh",
+                  "paper_1406_1717_gb300/csrc/mf_tilesort.cuh",
                   "paper_1406_1717_gb300/csrc/mf_pipeline.cu",
                   "paper_1406_1717_gb300/csrc/mf_sortlist.cu"]
 # CUDA kernel behind each timed group of the headline workload (4-byte

@@ -95,7 +95,7 @@ mf_status mf_set_stream(mf_handle h, void* cuda_stream);
 /* Median filter of one signal (paper Section 1; method Sections 3-6).
  *  x       device pointer, n elements of `dtype` (input, not modified)
  *  n       signal length, n >= k
- *  k       odd window size, 1 <= k <= n and k <= 262,143.  Below 5001
+ *  k       odd window size, 1 <= k <= n and k <= 262,143.  Below 3001
  *          (the handle's tier threshold, see mf_set_tier_threshold; at most
  *          9,344 for 4-byte and about 5,800 for 8-byte elements, one block
  *          pair in shared memory) the shared-memory pipeline runs; from it
@@ -194,7 +194,7 @@ mf_status mf_filter_backward_rows(mf_handle h, const float* gy, const int32_t* a
  *  cuda_stream         cudaStream_t to run on (NULL = legacy default stream)
  * Limits: k <= 9,344 (larger windows return MF_ERR_UNSUPPORTED).  The call
  * always runs the shared-memory pipeline: the tier threshold of
- * mf_set_tier_threshold does not apply, so for 5,001 <= k <= 9,344, where
+ * mf_set_tier_threshold does not apply, so for 3,001 <= k <= 9,344, where
  * mf_filter uses the large-k tier by default, the results are the same but
  * the time and the scratch differ.  The scratch a call needs is the larger
  * of 12 * kp bytes per block of k samples plus 6 * kp per block pair, and
@@ -287,7 +287,7 @@ mf_status mf_release_workspace(mf_handle h);
 
 /* Window size from which calls on this handle use the large-k tier instead
  * of the shared-memory pipeline (k >= k_large_from; k above the pipeline's
- * limit of 9,344 always uses it).  0 restores the built-in crossover (5001,
+ * limit of 9,344 always uses it).  0 restores the built-in crossover (3001,
  * measured on GB300); values above the pipeline's limit are capped to it.  Both tiers give the same results; the threshold only
  * chooses the faster one (the autotuner in paper_1406_1717_gb300/tune.py
  * measures the crossover).  Errors: MF_ERR_NULL, MF_ERR_K_GT_N (k < 0). */

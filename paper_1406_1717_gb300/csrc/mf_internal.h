@@ -127,10 +127,12 @@ cudaError_t launch_pipeline_batched(const void* x, void* y, int32_t* argmed, Ele
 constexpr int kLargeMaxK = (1 << 18) - 1;      // window-rank bitsets fit in shared memory
 constexpr int kLargeSegSteps = 1024;   // target steps per chain segment
 constexpr int kLargeMaxSegs = 32;      // segments per block pair at most
-// Default tier crossover: on GB300 (n = 10^7, random-walk and uniform
-// float32) the large-k tier is faster than the shared-memory pipeline from
-// k of about 5000 (4095: 4.4 vs 5.6 ms; 6001: 7.2 vs 5.9 ms).
-constexpr int kLargeFromK = 5001;
+// Default tier crossover, measured on GB300 (float32 random walk, ms,
+// pipeline / large-k tier): n = 10^7: k = 3001 2.01 / 2.08, 3501 2.18 /
+// 2.21, 4001 2.64 / 2.20; n = 10^6: 3001 0.69 / 0.56; n = 10^5: 3001 0.59 /
+// 0.43.  A batch of 4096 signals with k up to 4095 took 12.24 ms with the
+// crossover at 3001 and 12.60 ms at 5001.
+constexpr int kLargeFromK = 3001;
 cudaError_t large_setup();
 size_t large_workspace_bytes(int64_t n, int k, bool wide);
 cudaError_t launch_large(const void* x, int64_t n, int k, int rank, Elem el, void* y,

@@ -25,8 +25,11 @@ DEV = torch.device("cuda:0")
 
 @pytest.fixture(scope="module")
 def handle():
+    # every window up to the shared-memory pipeline's limit runs on the
+    # pipeline here (the large-k tier has tests of its own)
     mf.load_library()
     h = mf.mf_create(0, torch.cuda.current_stream(DEV))
+    mf.mf_set_tier_threshold(h, 1 << 30)
     yield h
     mf.mf_destroy(h)
 
