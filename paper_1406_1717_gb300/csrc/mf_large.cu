@@ -6,23 +6,26 @@
 // with 32-bit indices and the data in global memory:
 //
 //   large_chunk_sort  a warp sorts each 1024-element chunk of a block in
-//                     shared memory (stable LSD radix, Section 6.1)
+//                     shared memory, stably (Section 5.2): 4-byte keys by the
+//                     warp tile merge sort of key : index composites,
+//                     8-byte keys by a warp LSD radix sort (Section 6.1)
 //   large_merge       global merge-path tiers: sorted runs of R -> 2R until a
 //                     run covers the block, left run first on equal keys
 //   large_ranks       rank of each position in its block
-//   large_jrank       joint ranks of each pair by binary search in the other
-//                     block: ja / jb by position, jrs by B's sorted order and
-//                     M = the merged order
+//   large_jrank       joint ranks of each pair by a merge of its two sorted
+//                     blocks (A first on equal keys): ja / jb by position,
+//                     jrs by B's sorted order and M = the merged order
 //   large_unwind      unwind(B)'s links (Section 4: after unwind, undelete(B, i)
 //                     relinks i between its nearest smaller and larger
-//                     elements among positions < i); one CTA per run of
-//                     positions, seeded with a rank bitset of the positions
-//                     before the run
+//                     elements among positions < i); one CTA per eight runs
+//                     of positions, seeded with a rank bitset of the
+//                     positions before its first run
 //   large_seginit     rebuilds the lists before step i0 of a pair (Section 6.3
 //                     invariant: S_A u S_B are the h smallest of the window)
 //                     in one coalesced pass over the pair's merged order
 //   large_chain       the steps i0 .. i1-1 of Section 6.2 from that state,
-//                     one thread per (pair, segment), lists in global memory
+//                     one thread per (pair, segment), lists in global memory,
+//                     one level of independent node loads per step
 //   large_epilogue    node -> input element, y / argmed
 //
 // Nodes are numbered by joint rank: the element of joint rank r is node r,
@@ -30,7 +33,7 @@
 // small" and peek(A) <= peek(B) compare node numbers, and list neighbours are
 // rank neighbours: the walks of the two m pointers stay within a few cache
 // lines, and the only random load of a step (the deleted node, known in
-// advance) is prefetched.
+// advance) is prefetched into L2.
 // The serial depth of one pair is k steps; splitting the k steps of a pair
 // into S independent segments, each starting from a state rebuilt with O(k)
 // parallel work, cuts the depth to k / S at the price of S private copies of
