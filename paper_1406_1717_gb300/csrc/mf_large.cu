@@ -6,9 +6,10 @@
 // with 32-bit indices and the data in global memory:
 //
 //   large_chunk_sort  a warp sorts each 1024-element chunk of a block in
-//                     shared memory, stably (Section 5.2): 4-byte keys by the
-//                     warp tile merge sort of key : index composites,
-//                     8-byte keys by a warp LSD radix sort (Section 6.1)
+//                     shared memory, stably (Section 5.2), by the warp tile
+//                     merge sort of key : index composites (8-byte keys: on
+//                     their top 44 bits, the chunk sorted again on the whole
+//                     key when two of them tie there)
 //   large_merge       global merge-path tiers: sorted runs of R -> 2R until a
 //                     run covers the block, left run first on equal keys
 //   large_ranks       rank of each position in its block
@@ -167,10 +168,11 @@ __device__ __forceinline__ int bits_last_before(const uint32_t* W, const uint32_
 }
 
 // ---------------------------------------------------------------------------
+// a warp's shared memory: the padded tile of composites, plus 4 KB of
+// permutation scratch for the whole-key re-sort of 8-byte chunks
 template <typename KeyT>
-__host__ __device__ constexpr size_t chunk_warp_bytes() { return (size_t)kChunk * (2 * sizeof(KeyT) + 4) + 1024; }
-static_assert(kChunk == kTileElems && 8 * kTileU64 <= (int)chunk_warp_bytes<uint32_t>(),
-              "a 4-byte chunk is one warp tile of composites");
+__host__ __device__ constexpr size_t chunk_warp_bytes() { return 8ull * kTileU64 + (sizeof(KeyT) == 8 ? 4096 : 0); }
+static_assert(kChunk == kTileElems, "a chunk is one warp tile of composites");
 
 template <typename KeyT>
 __global__ void __launch_bounds__(256, 2)
@@ -189,11 +191,6 @@ large_chunk_sort(LargeTable tab, int64_t items)
     const int cnt = min(kChunk, NB - lo);
     if (cnt <= 0) return;
     unsigned char* ws = smem + (size_t)warp * chunk_warp_bytes<KeyT>();
-    KeyT* ka = reinterpret_cast<KeyT*>(ws);
-    KeyT* kb = ka + kChunk;
-    uint16_t* va = reinterpret_cast<uint16_t*>(kb + kChunk);
-    uint16_t* vb = va + kChunk;
-    uint32_t* hist = reinterpret_cast<uint32_t*>(vb + kChunk);
     const KeyT* xs = reinterpret_cast<const KeyT*>(p.x) + b * (int64_t)p.k + lo;
     if constexpr (sizeof(KeyT) == 4) {
         // 4-byte keys: the warp merge sort of composites key : index in the
@@ -212,19 +209,39 @@ large_chunk_sort(LargeTable tab, int64_t items)
         for (int i = 0; i < 32; ++i) {
             const int t = lane + 32 * i;
             if (t < cnt) {
-                const uint64_t c = T[tix(t)];
-                keys[o + t] = (KeyT)(c >> 10);
-                p.valA[o + t] = (uint32_t)lo + (uint32_t)(c & 1023u);
+                const uint64_t cp = T[tix(t)];
+                keys[o + t] = (KeyT)(cp >> 10);
+                p.valA[o + t] = (uint32_t)lo + (uint32_t)(cp & 1023u);
             }
         }
-        return;
+    } else {
+        // 8-byte keys: the same sort on the top 44 bits of the key; a chunk
+        // with ties in them is sorted again on the whole key (perm scratch:
+        // 4 KB after the tile)
+        uint64_t* T = reinterpret_cast<uint64_t*>(ws);
+        uint64_t v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {                  // coalesced: the network takes any 32
+            const int t = lane + 32 * i;
+            v[i] = t < cnt ? ((to_key(__ldg(xs + t), p.is_float) >> 20) << 10) | (uint64_t)t : kPadComp;
+        }
+        tile_sort(T, v, lane);
+        // one "block" of kChunk elements: block field 0 (x / kChunk by magic 2^22)
+        if (tile_has_wide_ties(T, cnt, lane))
+            tile_resort_wide(T, xs, p.is_float, cnt, kChunk, 1ull << 22,
+                             reinterpret_cast<uint16_t*>(ws + 8 * kTileU64), lane);
+        const int64_t o = b * p.kp + lo;
+        KeyT* keys = reinterpret_cast<KeyT*>(p.keyA);
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+            const int t = lane + 32 * i;
+            if (t < cnt) {
+                const uint32_t e = (uint32_t)(T[tix(t)] & 1023u);
+                keys[o + t] = (KeyT)to_key(__ldg(xs + e), p.is_float);
+                p.valA[o + t] = (uint32_t)lo + e;
+            }
+        }
     }
-    for (int t = lane; t < cnt; t += 32) { ka[t] = to_key(__ldg(xs + t), p.is_float); va[t] = (uint16_t)t; }
-    __syncwarp();
-    warp_sort_group<KeyT>(ka, va, kb, vb, cnt, 0, kChunk, 1, hist);
-    const int64_t o = b * p.kp + lo;
-    KeyT* keys = reinterpret_cast<KeyT*>(p.keyA);
-    for (int t = lane; t < cnt; t += 32) { keys[o + t] = ka[t]; p.valA[o + t] = (uint32_t)lo + va[t]; }
 }
 
 // sorted runs [l0, l0+R) and [l0+R, l0+2R) of every block -> one run; each

@@ -12,6 +12,7 @@
 // sorting the pairs (alpha[i], i) gives a stable order).
 #pragma once
 #include <cstdint>
+#include "mf_device.cuh"
 #include "mf_internal.h"
 
 namespace mf {
@@ -126,6 +127,106 @@ __device__ __forceinline__ void tile_sort(uint64_t* T, uint64_t (&v)[32], int la
         for (int i = 0; i < 32; ++i) T[tix(o0 + i)] = v[i];
         __syncwarp();
     }
+}
+
+// x / d by a multiply-shift with magic = ceil(2^32 / d); exact for the
+// ranges the kernels use (x < 8,192, 1 <= d <= 1,024), which
+// tests/test_index_arithmetic.py checks exhaustively
+__device__ __forceinline__ uint32_t udiv(uint32_t x, uint64_t magic)
+{
+    return (uint32_t)(((uint64_t)x * magic) >> 32);
+}
+
+// Composite layouts.  4-byte elements: block : 32-bit key : position (22, 32
+// and 10 bits).  8-byte elements: block : top 44 bits of the 64-bit key :
+// position (10, 44, 10); the key's low 20 bits decide only between elements
+// whose top 44 bits are equal.
+template <bool WIDE> struct Comp {
+    static constexpr int kBlk = WIDE ? 54 : 42;         // shift of the block field
+    __device__ __forceinline__ static uint64_t key(uint64_t c)
+    {
+        return (c >> 10) & ((1ull << (kBlk - 10)) - 1ull);
+    }
+    __device__ __forceinline__ static int blk(uint64_t c) { return (int)(c >> kBlk); }
+};
+
+// Does the sorted tile hold two adjacent composites with equal block and
+// top 44 key bits (8-byte layout)?  Warp-uniform.
+__device__ __forceinline__ bool tile_has_wide_ties(const uint64_t* T, int tile_n, int lane)
+{
+    bool tie = false;
+    uint64_t prev = T[tix(32 * lane)] >> 10;
+#pragma unroll 4
+    for (int i = 1; i <= 32; ++i) {
+        const int t = 32 * lane + i;
+        if (t < tile_n) {
+            const uint64_t cur = T[tix(t)] >> 10;
+            tie = tie || cur == prev;
+            prev = cur;
+        }
+    }
+    return __any_sync(0xffffffffu, tie);
+}
+
+// 8-byte elements whose tile has two elements of one block with equal top 44
+// key bits: sort the tile again, least significant digit first (stable LSD on
+// the low 32 and the top 44 bits): by (block, low 32 bits, position), then by
+// (block, top 44 bits, rank after that sort), and put the positions back in
+// the low field.  perm1 / r1: the first sort's permutation and its inverse,
+// in 4 KB of shared memory that the caller does not use until later.
+static __device__ __noinline__ void tile_resort_wide(uint64_t* T, const uint64_t* xt, bool is_float, int tile_n,
+                                              int k, uint64_t kmagic, uint16_t* perm1, int lane)
+{
+    using C = Comp<true>;
+    uint16_t* r1 = perm1 + 1024;
+    uint64_t v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int et = 32 * lane + ((i + lane) & 31);
+        uint64_t c = kPadComp;
+        if (et < tile_n) {
+            const uint32_t blk = udiv((uint32_t)et, kmagic);
+            const uint32_t lo = (uint32_t)to_key(__ldg(xt + et), is_float);
+            c = ((uint64_t)blk << C::kBlk) | ((uint64_t)lo << 10) | ((uint32_t)et - blk * (uint32_t)k);
+        }
+        v[i] = c;
+    }
+    __syncwarp();                                       // the caller's reads of T are done
+    tile_sort(T, v, lane);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int t = lane + 32 * i;
+        const uint64_t c = T[tix(t)];
+        if (t < tile_n) {
+            const int e = C::blk(c) * k + (int)(c & 1023u);
+            perm1[t] = (uint16_t)e;
+            r1[e] = (uint16_t)t;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int et = 32 * lane + ((i + lane) & 31);
+        uint64_t c = kPadComp;
+        if (et < tile_n) {
+            const uint32_t blk = udiv((uint32_t)et, kmagic);
+            const uint64_t top = to_key(__ldg(xt + et), is_float) >> 20;
+            c = ((uint64_t)blk << C::kBlk) | (top << 10) | r1[et];
+        }
+        v[i] = c;
+    }
+    __syncwarp();
+    tile_sort(T, v, lane);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int x = lane + 32 * i;
+        const uint64_t c = T[tix(x)];
+        if (x < tile_n) {
+            const int e = perm1[c & 1023u];
+            T[tix(x)] = (c & ~1023ull) | (uint64_t)(e - C::blk(c) * k);
+        }
+    }
+    __syncwarp();
 }
 
 }  // namespace mf
