@@ -9,7 +9,9 @@
 // so lane-major stores and the merge write-backs are free of bank conflicts.
 // Composites are distinct, so ascending order of composites is a stable sort
 // of whatever key they carry in their high bits (Section 5.2 of the paper:
-// sorting the pairs (alpha[i], i) gives a stable order).
+// sorting the pairs (alpha[i], i) gives a stable order).  8-byte keys carry
+// their top 44 bits; a tile in which two of those tie within a block is
+// sorted again on the whole key (tile_has_wide_ties, tile_resort_wide).
 #pragma once
 #include <cstdint>
 #include "mf_device.cuh"
