@@ -57,7 +57,7 @@ typedef enum {
     MF_ERR_DTYPE = 5,        /* unknown mf_dtype                                    */
     MF_ERR_OOM = 6,          /* workspace above max_workspace_bytes, or malloc fail */
     MF_ERR_CUDA = 7,         /* a CUDA runtime call or kernel failed                */
-    MF_ERR_UNSUPPORTED = 8,  /* valid request this build does not implement         */
+    MF_ERR_UNSUPPORTED = 8,  /* valid request this library variant does not serve  */
     MF_ERR_OVERLAP = 9,      /* an output buffer overlaps an input buffer           */
     MF_ERR_DEVICE = 10,      /* device index invalid or not an sm_103 GPU           */
     MF_ERR_BAD_SEGMENT = 11, /* a batched segment descriptor is invalid             */

@@ -612,7 +612,7 @@ const char* mf_status_str(mf_status s) {
         case MF_ERR_DTYPE: return "MF_ERR_DTYPE: unknown dtype";
         case MF_ERR_OOM: return "MF_ERR_OOM: workspace allocation failed or above the cap";
         case MF_ERR_CUDA: return "MF_ERR_CUDA: a CUDA call or kernel failed";
-        case MF_ERR_UNSUPPORTED: return "MF_ERR_UNSUPPORTED: not implemented in this build";
+        case MF_ERR_UNSUPPORTED: return "MF_ERR_UNSUPPORTED: not served by this library variant";
         case MF_ERR_OVERLAP: return "MF_ERR_OVERLAP: output overlaps an input";
         case MF_ERR_DEVICE: return "MF_ERR_DEVICE: no such device or not compute capability 10.3";
         case MF_ERR_BAD_SEGMENT: return "MF_ERR_BAD_SEGMENT: invalid batched segment descriptor";
